@@ -1,0 +1,274 @@
+"""Python face of the FP64 CPU oracle (CaRtGS, arXiv 2410.00486).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
+baseline leg are the only users.  The library path never imports this module.
+
+The render, gradient and statistics steps call the plain C implementation in
+cgs_oracle.c (double precision, one pixel / one Gaussian at a time).  Adam, the
+opacity regulariser and the adaptive keyframe scheduler are written here in
+numpy / plain Python, step by step from the paper:
+
+  * opacity regularisation, Eqs. 10-11 (Sec. III-C.3)
+  * Adam with the 3DGS hyper-parameters the paper keeps (Sec. IV-A)
+  * adaptive optimisation scheduler, Eqs. 5-8 (Sec. III-C.2)
+
+Parity status: every function here is pinned by tests/test_oracle_*.py
+(closed forms, invariants, finite differences, scipy's spherical harmonics,
+torch.optim.Adam, brute-force enumeration); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "cgs_oracle.c"
+_SO = _HERE / "_build" / "liboracle.so"
+
+NREC = 10
+NCAM = 17
+REC_FIELDS = ("u", "v", "conA", "conB", "conC", "opacity", "r", "g", "b", "depth")
+
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile the C oracle with gcc (no FMA contraction, so each formula rounds as written)."""
+    if force or not _SO.exists() or _SO.stat().st_mtime < _SRC.stat().st_mtime:
+        _SO.parent.mkdir(parents=True, exist_ok=True)
+        tmp = _SO.with_suffix(f".{os.getpid()}.tmp")
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                        "-o", str(tmp), str(_SRC), "-lm"], check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(str(_SO))
+        P = ctypes.c_void_p
+        i32, i64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        lib.orc_preprocess.argtypes = [P, i64, i32, P, i32, i32, i32, i32, f64, f64, P, P, P, P, P]
+        lib.orc_bin.argtypes = [P, P, P, P, i32, i64, i32, i32, i32, i64, P, P]
+        lib.orc_bin.restype = i64
+        lib.orc_render_fwd.argtypes = [P, P, P, i32, i32, i32, i32, P, P, P, P, f64, f64,
+                                       P, P, P, P, P, P, P, P]
+        lib.orc_render_bwd.argtypes = [P, P, P, i32, i64, i32, i32, i32, P, P, P, P, P, P, P,
+                                       f64, P]
+        lib.orc_preprocess_bwd.argtypes = [P, i64, i32, P, i32, i32, i32, i32, f64, P, P]
+        lib.orc_densify_stats.argtypes = [P, P, i32, i64, i32, i32, P, P, P]
+        lib.orc_sh_basis.argtypes = [i32, f64, f64, f64, P, P]
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def cams_to_oracle(cams: np.ndarray) -> np.ndarray:
+    """float32[V][20] camera rows -> double[V][17] (R, t, fx, fy, cx, cy, weight)."""
+    cams = np.asarray(cams)
+    return _f64(cams[:, :17])
+
+
+def sh_basis(deg: int, d) -> tuple[np.ndarray, np.ndarray]:
+    lib = _load()
+    Y = np.zeros(16)
+    dY = np.zeros(48)
+    lib.orc_sh_basis(deg, float(d[0]), float(d[1]), float(d[2]), _p(Y), _p(dY))
+    return Y, dY.reshape(16, 3)
+
+
+def preprocess(params, n, deg, cams, W, H, B, near=0.2, tol_px=5e-4) -> dict:
+    lib = _load()
+    P = _f64(params)
+    C = cams_to_oracle(cams)
+    V = C.shape[0]
+    m = V * n
+    out = dict(rec=np.zeros((m, NREC)), radius=np.zeros(m, np.int32),
+               rect=np.zeros((m, 4), np.int32), clamp=np.zeros(m, np.int32),
+               fragile=np.zeros(m, np.int32))
+    lib.orc_preprocess(_p(P), n, deg, _p(C), V, W, H, B, near, tol_px, _p(out["rec"]),
+                       _p(out["radius"]), _p(out["rect"]), _p(out["clamp"]), _p(out["fragile"]))
+    return out
+
+
+def tiles(W, H, B):
+    return (W + B - 1) // B, (H + B - 1) // B
+
+
+def bin_lists(u, v, z, radius, V, n, W, H, B):
+    """Tile lists ordered by (tile, depth, slot): returns (ranges[Ttot, 2], vals[count])."""
+    lib = _load()
+    Tx, Ty = tiles(W, H, B)
+    Ttot = V * Tx * Ty
+    u, v, z = _f64(u), _f64(v), _f64(z)
+    radius = np.ascontiguousarray(radius, np.int32)
+    ranges = np.zeros((Ttot, 2), np.uint32)
+    cnt = lib.orc_bin(_p(u), _p(v), _p(z), _p(radius), V, n, W, H, B, 0, _p(ranges), None)
+    vals = np.zeros(max(1, cnt), np.uint32)
+    cnt2 = lib.orc_bin(_p(u), _p(v), _p(z), _p(radius), V, n, W, H, B, vals.size, _p(ranges),
+                       _p(vals))
+    assert cnt2 == cnt
+    return ranges, vals[:cnt]
+
+
+def render_fwd(rec, ranges, vals, V, W, H, B, cams, bg=(0.0, 0.0, 0.0), tgt_rgb=None,
+               tgt_depth=None, lambda_d=0.1, tol=0.0, want_hash=False) -> dict:
+    lib = _load()
+    rec = _f64(rec)
+    C = cams_to_oracle(cams)
+    bgv = _f64(bg)
+    HW = H * W
+    out = dict(img=np.zeros((V, 3, H, W)), depth=np.zeros((V, H, W)), T=np.zeros((V, H, W)),
+               last=np.zeros((V, H, W), np.uint32), loss_view=np.zeros(V),
+               depth_count=np.zeros(V, np.int64), near=np.zeros((V, H, W), np.int32))
+    h = np.zeros(1, np.uint64)
+    tr = _f64(tgt_rgb) if tgt_rgb is not None else None
+    td = _f64(tgt_depth) if tgt_depth is not None else None
+    lib.orc_render_fwd(_p(rec), _p(np.ascontiguousarray(ranges, np.uint32)),
+                       _p(np.ascontiguousarray(vals, np.uint32)), V, W, H, B, _p(bgv), _p(C),
+                       _p(tr) if tr is not None else None, _p(td) if td is not None else None,
+                       lambda_d, tol, _p(out["img"]), _p(out["depth"]), _p(out["T"]),
+                       _p(out["last"]), _p(out["loss_view"]), _p(out["depth_count"]),
+                       _p(out["near"]), _p(h) if want_hash else None)
+    del HW
+    if want_hash:
+        out["hash"] = int(h[0])
+    return out
+
+
+def render_bwd(rec, ranges, vals, V, n, W, H, B, cams, img, depth, tgt_rgb, tgt_depth,
+               depth_count, bg=(0.0, 0.0, 0.0), lambda_d=0.1) -> np.ndarray:
+    lib = _load()
+    grads = np.zeros((V * n, NREC))
+    td = _f64(tgt_depth) if tgt_depth is not None else None
+    lib.orc_render_bwd(_p(_f64(rec)), _p(np.ascontiguousarray(ranges, np.uint32)),
+                       _p(np.ascontiguousarray(vals, np.uint32)), V, n, W, H, B, _p(_f64(bg)),
+                       _p(cams_to_oracle(cams)), _p(_f64(img)), _p(_f64(depth)), _p(_f64(tgt_rgb)),
+                       _p(td) if td is not None else None,
+                       _p(np.ascontiguousarray(depth_count, np.int64)), lambda_d, _p(grads))
+    return grads
+
+
+def preprocess_bwd(params, n, deg, cams, W, H, B, slot_grads, near=0.2) -> np.ndarray:
+    lib = _load()
+    P = _f64(params)
+    out = np.zeros_like(P)
+    C = cams_to_oracle(cams)
+    lib.orc_preprocess_bwd(_p(P), n, deg, _p(C), C.shape[0], W, H, B, near,
+                           _p(_f64(slot_grads)), _p(out))
+    return out
+
+
+def densify_stats(slot_grads, radius, V, n, W, H, accum=None, denom=None, max_r2d=None):
+    lib = _load()
+    accum = np.zeros(n) if accum is None else _f64(accum).copy()
+    denom = np.zeros(n) if denom is None else _f64(denom).copy()
+    max_r2d = np.zeros(n) if max_r2d is None else _f64(max_r2d).copy()
+    lib.orc_densify_stats(_p(_f64(slot_grads)), _p(np.ascontiguousarray(radius, np.int32)), V, n,
+                          W, H, _p(accum), _p(denom), _p(max_r2d))
+    return accum, denom, max_r2d
+
+
+# --------------------------------------------------------------- loss pieces
+
+def opacity_reg(params, n, lambda_o):
+    """L_o = (1/N) sum_i |o_i| with o_i = sigmoid(opacity logit) > 0 (Eq. 10), weighted by
+    lambda_o (Eq. 11).  Returns (lambda_o * L_o, gradient w.r.t. the logits)."""
+    x = _f64(params)[10 * n: 11 * n]
+    o = 1.0 / (1.0 + np.exp(-x))
+    return lambda_o * o.sum() / n, lambda_o * o * (1.0 - o) / n
+
+
+def adam(theta, grad, m, v, step, lr_per_elem, beta1=0.9, beta2=0.999, eps=1e-15):
+    """One Adam step with bias correction (t starts at 1); every element is updated,
+    including those with zero gradient (reading).  Returns new (theta, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    mhat = m / (1.0 - beta1 ** step)
+    vhat = v / (1.0 - beta2 ** step)
+    return theta - lr_per_elem * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def lr_per_element(n, deg, lr6):
+    """Expand the six per-group learning rates to the flat parameter layout."""
+    K = (deg + 1) ** 2
+    sizes = [3 * n, 3 * n, 4 * n, n, 3 * n, 3 * (K - 1) * n]
+    return np.concatenate([np.full(s, float(l)) for s, l in zip(sizes, lr6)])
+
+
+def iteration(params, n, deg, cams, W, H, B, tgt_rgb, tgt_depth, bg=(0.0, 0.0, 0.0),
+              lambda_d=0.1, lambda_o=0.0, near=0.2, tol=0.0) -> dict:
+    """Loss and parameter gradient of one window iteration, plus every intermediate."""
+    V = np.asarray(cams).shape[0]
+    pre = preprocess(params, n, deg, cams, W, H, B, near)
+    rec = pre["rec"]
+    ranges, vals = bin_lists(rec[:, 0], rec[:, 1], rec[:, 9], pre["radius"], V, n, W, H, B)
+    fw = render_fwd(rec, ranges, vals, V, W, H, B, cams, bg, tgt_rgb, tgt_depth, lambda_d, tol)
+    sg = render_bwd(rec, ranges, vals, V, n, W, H, B, cams, fw["img"], fw["depth"], tgt_rgb,
+                    tgt_depth, fw["depth_count"], bg, lambda_d)
+    grads = preprocess_bwd(params, n, deg, cams, W, H, B, sg, near)
+    lo, glo = opacity_reg(params, n, lambda_o)
+    grads[10 * n: 11 * n] += glo
+    return dict(pre=pre, ranges=ranges, vals=vals, fwd=fw, slot_grads=sg, grads=grads,
+                loss=float(fw["loss_view"].sum() + lo), loss_o=lo)
+
+
+# ------------------------------------------------------ adaptive scheduler
+
+class Scheduler:
+    """Adaptive keyframe selection, Eqs. 5-8 (Sec. III-C.2), step by step.
+
+    Readings: a new keyframe's loss starts at +inf (it is never read before the
+    keyframe is trained once, since r0 >= 1); d_k = max(1, floor(k / d)); ties in the
+    top-d_k selection go to the lower index; a draw picks uniformly among keyframes
+    with r_i > 0 using a caller-supplied uniform 32-bit integer (index = u mod count
+    into the ascending list of eligible keyframes).
+    """
+
+    def __init__(self, d: int = 4):
+        self.d = d
+        self.K: list[int] = []       # keyframe ids (Eq. 5)
+        self.R: list[int] = []       # remaining iterations (Eq. 6)
+        self.L: list[float] = []     # last loss (Eq. 7)
+
+    def add(self, keyframe_id: int, r0: int):
+        self.K.append(keyframe_id)
+        self.R.append(int(r0))
+        self.L.append(float("inf"))
+
+    def _refill(self):
+        """Eq. 8: r_i = 2 for the d_k largest losses, 1 otherwise."""
+        k = len(self.K)
+        dk = max(1, k // self.d)
+        order = sorted(range(k), key=lambda i: (-self.L[i], i))
+        top = set(order[:dk])
+        self.R = [2 if i in top else 1 for i in range(k)]
+
+    def draw(self, rand_u32: int) -> int:
+        """Pick a pool index with r > 0 (refilling first if none is left); r -= 1."""
+        if not self.K:
+            raise ValueError("empty keyframe pool")
+        elig = [i for i, r in enumerate(self.R) if r > 0]
+        if not elig:
+            self._refill()
+            elig = [i for i, r in enumerate(self.R) if r > 0]
+        i = elig[int(rand_u32) % len(elig)]
+        self.R[i] -= 1
+        return i
+
+    def report(self, index: int, loss: float):
+        self.L[index] = float(loss)
