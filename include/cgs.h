@@ -1,0 +1,271 @@
+/*
+ * cgs.h -- C ABI of libcgs: one differentiable 3D Gaussian Splatting mapping
+ * iteration over a window of keyframes, as used by the photorealistic mapping
+ * back-end of CaRtGS (arXiv 2410.00486, Sec. III-B / III-C), for NVIDIA GB300
+ * (sm_103a).
+ *
+ * Problem statement (Sec. III-B): Gaussians G = {p, q, s, sigma, SH} and a window
+ * of keyframes (pose, observed RGB image, optional depth) are given; render each
+ * keyframe by alpha blending (Eq. 1), measure the L1 photometric + depth loss
+ * (the L1 part of Eq. 9, the opacity term of Eqs. 10-11) and take one optimiser
+ * step on G.  The adaptive keyframe schedule (Eqs. 5-8) runs on the host.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All pointers marked "device" are CUDA device pointers owned by the caller.
+ *    The library never allocates, frees or synchronises device memory; it only
+ *    enqueues kernels and memsets on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream).  Nothing is allocated inside the calls, so the whole
+ *    iteration can be captured into a CUDA graph by the caller.
+ *  - Return value: synchronous argument validation and launch status
+ *    (CGS_OK, CGS_ERR_ARG, CGS_ERR_WORKSPACE, CGS_ERR_CUDA).  Conditions found
+ *    on the device are written to `*status_dev` (device int32, caller clears
+ *    it to 0; first error wins) and read by the caller after synchronising:
+ *    CGS_ERR_CAPACITY, CGS_ERR_NONFINITE.  No kernel traps or asserts.
+ *  - A "slot" is one (view v, Gaussian g) pair, index v*n + g, 0 <= v < V.
+ *  - All floating-point data is float32.
+ *
+ * Parameter vector (device float[cgs_param_count(n, sh_degree)]), groups in order:
+ *    means[n][3] | log_scales[n][3] | quats[n][4] (w, x, y, z, unnormalised) |
+ *    opacity_logits[n] | sh_dc[n][3] | sh_rest[n][K-1][3],   K = (sh_degree+1)^2
+ *  Activations (Sec. III-B parameters p, q, s, sigma): s = exp(log_scale),
+ *  q normalised, opacity = sigmoid(logit), colour = SH(dir) + 0.5 clamped below 0.
+ *
+ * Projected record of a slot (device float[V*n][CGS_REC_FLOATS], 16-byte aligned):
+ *    [0] u  [1] v      projected centre, pixel (x, y) centred on integer (x, y)
+ *    [2] A  [3] B  [4] C   conic (inverse 2-D covariance): power = -(A dx^2 + C dy^2)/2 - B dx dy
+ *    [5] opacity  [6] depth (camera z)  [7] radius as int32 bits (0 = culled)
+ *    [8] r  [9] g  [10] b  [11] colour clamp mask as int32 bits (bit c = channel c clamped)
+ * Slot gradient (device float[V*n][CGS_REC_FLOATS]): dL/d(field) at the same
+ * index for fields 0-6 and 8-10; entries 7 and 11 are unused (kept zero).
+ */
+#ifndef CGS_H
+#define CGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CGS_REC_FLOATS 12
+
+enum cgs_status {
+    CGS_OK = 0,
+    CGS_ERR_ARG = -1,        /* invalid argument (null pointer, size, alignment, unsupported option) */
+    CGS_ERR_WORKSPACE = -2,  /* workspace smaller than the matching *_workspace() query */
+    CGS_ERR_CUDA = -3,       /* a CUDA launch or memset returned an error */
+    CGS_ERR_CAPACITY = -4,   /* device: tile instances exceeded the capacity; lists were truncated */
+    CGS_ERR_NONFINITE = -5,  /* device: the loss of a view was NaN or infinite */
+    CGS_ERR_TIMEOUT = -6     /* reserved: a bounded device-side wait gave up (no call waits today) */
+};
+
+/* One keyframe's pinhole camera: world -> camera x_c = R x_w + t, camera axes x right,
+ * y down, z forward; pixel = (fx x_c/z_c + cx, fy y_c/z_c + cy).  80 bytes. */
+typedef struct {
+    float R[9];          /* row-major rotation */
+    float t[3];          /* translation */
+    float fx, fy, cx, cy;
+    float loss_weight;   /* not read by the kernels: view weights are passed as view_weight */
+    float pad[3];
+} cgs_camera;
+
+/* Settings shared by every view of a window (host struct, read at call time). */
+typedef struct {
+    int32_t width, height;   /* image size in pixels, identical for all views */
+    int32_t tile;            /* tile edge B: 8, 16 or 32 */
+    int32_t batch_depth;     /* splats staged per shared-memory batch in the raster kernels:
+                                32, 64, 128 or 256 */
+    int32_t sh_degree;       /* 0..3 */
+    float near_z;            /* near-plane cull: camera z must exceed this (0.2) */
+    float bg[3];             /* background colour added with the final transmittance */
+    float lambda_depth;      /* weight of the masked depth L1 term (0.1) */
+} cgs_config;
+
+/* Number of floats in the parameter vector: (14 + 3 (K-1)) n. */
+int64_t cgs_param_count(int64_t n, int32_t sh_degree);
+
+/* Number of tiles per view and for the whole window: ceil(W/B) ceil(H/B) (* V). */
+int64_t cgs_tiles_per_view(const cgs_config *cfg);
+
+/*
+ * cgs_preprocess -- projection of every Gaussian into every view of the window
+ * (the "projected 2D Gaussian" and colour c_k of Eq. 1, Sec. III-B; 3DGS EWA
+ * projection): per slot, camera-space mean, near-plane cull, 3-D covariance
+ * R diag(s^2) R^T, Jacobian of the perspective map (guard band 1.3 x half
+ * field of view), 2-D covariance + 0.3 I, conic, radius ceil(3 sqrt(lambda_max))
+ * (lambda_max = mid + sqrt(max(0.1, mid^2 - det))), tile rectangle (a slot with
+ * an empty rectangle is culled), SH colour at the view direction (+0.5, clamped
+ * at 0) and sigmoid opacity.  Each Gaussian's parameters are read once for all
+ * V views.
+ *   params    device, parameter vector (layout above), n Gaussians
+ *   cams      device, cgs_camera[V]
+ *   rec       device out, float[V*n][12] records (every slot's radius is written;
+ *             other fields only for visible slots)
+ *   slot_grad device out, float[V*n][12]; zeroed for every visible slot so the
+ *             backward can accumulate into it (may be NULL to skip)
+ * Errors: CGS_ERR_ARG for null/unaligned pointers, n < 1, V < 1, V*n >= 2^32,
+ * unsupported tile / sh_degree / sizes.
+ */
+int cgs_preprocess(const float *params, int64_t n, const cgs_camera *cams, int32_t V,
+                   const cgs_config *cfg, float *rec, float *slot_grad, int32_t *status_dev,
+                   void *stream);
+
+/*
+ * cgs_bin_sort -- tile binning: every visible slot is listed in each tile of its
+ * rectangle, and each tile's list is sorted by (depth, slot) ascending; tiles are
+ * numbered view-major (global tile = v*Tx*Ty + ty*Tx + tx), so the whole window
+ * shares one sort.  The order is the blending order of Eq. 1 (front to back);
+ * equal depths keep the Gaussian order.  Rectangle of a slot with centre (u, v)
+ * and radius r, in tile units, hi exclusive:
+ *   [clamp(floor((u-r)/B), 0, Tx), clamp(floor((u+r+B-1)/B), 0, Tx)) and likewise in y,
+ * evaluated exactly (u enters only through floor(u)).
+ * Method: a counting pass over tiles (the most significant radix digit, one per
+ * tile), a scatter into per-tile buckets, then a per-tile sort of the unique
+ * 64-bit keys (depth bits << 32 | slot) in shared memory.
+ *   rec        device, records from cgs_preprocess (u, v, depth, radius are read)
+ *   workspace  device scratch of at least cgs_bin_sort_workspace(capacity, V, cfg) bytes,
+ *              256-byte aligned
+ *   capacity   number of entries `vals` can hold
+ *   vals       device out, uint32[capacity]: slot ids, tile after tile
+ *   ranges     device out, uint32[2 * V * tiles_per_view]: [start, end) of each tile
+ *   tile_order device out (may be NULL), uint32[V * tiles_per_view]: tiles ordered
+ *              by decreasing list length (work order for the raster kernels)
+ *   n_inst_dev device out, int64: total number of tile instances (also when it
+ *              exceeds capacity; then lists are truncated and CGS_ERR_CAPACITY set)
+ */
+size_t cgs_bin_sort_workspace(int64_t capacity, int32_t V, const cgs_config *cfg);
+int cgs_bin_sort(const float *rec, int64_t n, int32_t V, const cgs_config *cfg, void *workspace,
+                 size_t workspace_bytes, int64_t capacity, uint32_t *vals, uint32_t *ranges,
+                 uint32_t *tile_order, int64_t *n_inst_dev, int32_t *status_dev, void *stream);
+
+/*
+ * cgs_render_fwd -- alpha blending of Eq. 1 (Sec. III-B; read with (1 - alpha_j)
+ * inside the product), front to back per pixel over its tile's list:
+ *   power = -(A dx^2 + C dy^2)/2 - B dx dy, (dx, dy) = (u - x, v - y); skip if power > 0;
+ *   alpha = min(0.99, opacity exp(power)); skip if alpha < 1/255;
+ *   stop before a splat that would take T (1 - alpha) below 1e-4;
+ *   img = sum c alpha T + T_final bg, depth = sum z alpha T.
+ * With targets, the L1 loss of Eq. 9 (lambda_ssim = 0) plus the depth term is fused:
+ *   L_v = w_v [ mean |img - tgt_rgb| + lambda_depth mean_{tgt_depth > 0} |depth - tgt_depth| ].
+ *   vals, ranges  from cgs_bin_sort;  tile_order may be NULL (natural order)
+ *   view_weight   device float[V] (w_v), may be NULL (all 1)
+ *   tgt_rgb       device float[V][3][H][W] or NULL (no loss);  tgt_depth float[V][H][W] or NULL
+ *   img float[V][3][H][W], depth float[V][H][W], t_final float[V][H][W],
+ *   last uint32[V][H][W] (1-based list position of the last blended splat, 0 = none)
+ *   loss_view     device float[V] out (only with targets)
+ *   depth_count   device int32[V] out: |{tgt_depth > 0}| per view (only with targets)
+ *   workspace     device scratch of cgs_render_fwd_workspace(V, cfg) bytes (required); on
+ *                 return it holds float[V * tiles_per_view][5] per-tile partial sums: sum |r_rgb|,
+ *                 sum |r_depth| over valid depth pixels, valid depth count, (splat, pixel)
+ *                 pairs evaluated, pairs blended (the last two are the blend's work counts)
+ */
+size_t cgs_render_fwd_workspace(int32_t V, const cgs_config *cfg);
+int cgs_render_fwd(const float *rec, const uint32_t *vals, const uint32_t *ranges,
+                   const uint32_t *tile_order, int32_t V, const cgs_config *cfg,
+                   const float *view_weight, const float *tgt_rgb, const float *tgt_depth,
+                   float *img, float *depth, float *t_final, uint32_t *last, float *loss_view,
+                   int32_t *depth_count, void *workspace, size_t workspace_bytes,
+                   int32_t *status_dev, void *stream);
+
+/*
+ * cgs_raster_bwd -- backward of the blend (Eqs. 2-4, Sec. III-C.1), pixel-parallel,
+ * back to front from `last`, with the transmittance recomputed from the stored
+ * final T (T_j = T_{j+1} / (1 - alpha_j)) instead of stored per-pixel lists.  Per
+ * blended (splat, pixel) pair, dL/d(u, v, A, B, C, opacity, rgb, depth); the 32
+ * pixels of a warp are summed with shuffles before one set of atomic adds per
+ * splat into slot_grad.  dL/dalpha is zero where alpha was clamped at 0.99.
+ * Pixel gradients come either from the fused L1 loss (dl_dimg == NULL: sign of the
+ * residual, 0 at 0, times w_v / (3 H W) and w_v lambda_depth / depth_count) or
+ * from the caller (dl_dimg float[V][3][H][W], dl_ddepth float[V][H][W] or NULL).
+ *   slot_grad  device in/out: accumulated (+=); zeroed by cgs_preprocess
+ */
+int cgs_raster_bwd(const float *rec, const uint32_t *vals, const uint32_t *ranges,
+                   const uint32_t *tile_order, int32_t V, const cgs_config *cfg,
+                   const float *view_weight, const float *img, const float *depth,
+                   const float *t_final, const uint32_t *last, const float *tgt_rgb,
+                   const float *tgt_depth, const int32_t *depth_count, const float *dl_dimg,
+                   const float *dl_ddepth, float *slot_grad, int32_t *status_dev, void *stream);
+
+/*
+ * cgs_preprocess_bwd -- chain rule from the slot gradients of every visible slot
+ * back to the parameters (position, log-scale, quaternion, opacity logit, SH),
+ * summed over the V views; the derivative of a guard-band-clamped Jacobian entry
+ * and of a clamped colour channel is 0.  When accum/denom/max_r2d are non-NULL
+ * the densification statistics of cgs_densify_stats are accumulated in the same
+ * pass.
+ *   param_grad device float[cgs_param_count]: overwritten (accumulate == 0) or added to
+ */
+int cgs_preprocess_bwd(const float *params, int64_t n, const cgs_camera *cams, int32_t V,
+                       const cgs_config *cfg, const float *rec, const float *slot_grad,
+                       float *param_grad, int32_t accumulate, float *accum, float *denom,
+                       float *max_r2d, int32_t *status_dev, void *stream);
+
+/* cgs_render_bwd -- cgs_raster_bwd followed by cgs_preprocess_bwd (same arguments). */
+int cgs_render_bwd(const float *params, int64_t n, const cgs_camera *cams, int32_t V,
+                   const cgs_config *cfg, const float *rec, const uint32_t *vals,
+                   const uint32_t *ranges, const uint32_t *tile_order, const float *view_weight,
+                   const float *img, const float *depth, const float *t_final,
+                   const uint32_t *last, const float *tgt_rgb, const float *tgt_depth,
+                   const int32_t *depth_count, const float *dl_dimg, const float *dl_ddepth,
+                   float *slot_grad, float *param_grad, int32_t accumulate, float *accum,
+                   float *denom, float *max_r2d, int32_t *status_dev, void *stream);
+
+/*
+ * cgs_densify_stats -- per-Gaussian statistics that guide adaptive densification
+ * (Sec. III-A.3 "guided by gradients and the size"; Sec. IV-A densify every 500
+ * iterations with tau_p = 0.001): for every visible slot of view v,
+ *   accum[g] += || (dL_v/du * W/2, dL_v/dv * H/2) ||   (view-space, NDC units),
+ *   denom[g] += 1,  max_r2d[g] = max(max_r2d[g], radius).
+ * Uses per-view gradients (slot_grad), never their sum over views.  Accumulates.
+ */
+int cgs_densify_stats(const float *rec, const float *slot_grad, int64_t n, int32_t V,
+                      const cgs_config *cfg, float *accum, float *denom, float *max_r2d,
+                      void *stream);
+
+/*
+ * cgs_adam -- fused optimiser step on the whole parameter vector (Adam with bias
+ * correction, the optimiser of the 3DGS training the paper keeps, Sec. IV-A), with
+ * the opacity regulariser of Eqs. 10-11 folded into the gradient:
+ *   g <- grad + lambda_o o (1 - o) / n on opacity logits (o = sigmoid(logit)),
+ *   m <- b1 m + (1-b1) g;  v <- b2 v + (1-b2) g^2;
+ *   p <- p - lr_group (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * Every element is updated (zero-gradient elements move by momentum).
+ *   lr        host float[6]: means, log_scales, quats, opacity, sh_dc, sh_rest
+ *   step      >= 1, the step number t used for bias correction, unless step_dev is given
+ *   step_dev  device int32 (may be NULL): when given, it is incremented on the device
+ *             and its new value is the step t (so a captured CUDA graph advances t at
+ *             every replay); `step` is then ignored
+ *   loss_o    device float (may be NULL): overwritten with lambda_o * mean(o) of the
+ *             parameters before the step (summed with float atomics: the last bits
+ *             depend on scheduling)
+ * params, grads, m, v: device float[cgs_param_count(n, sh_degree)].
+ */
+int cgs_adam(float *params, const float *grads, float *m, float *v, int64_t n,
+             int32_t sh_degree, const float *lr, float beta1, float beta2, float eps,
+             int32_t step, int32_t *step_dev, float lambda_o, float *loss_o, void *stream);
+
+/*
+ * Adaptive keyframe scheduler (Eqs. 5-8, Sec. III-C.2), host only.  A pool of
+ * keyframes with remaining iteration counts r_i and last losses l_i; a draw picks
+ * uniformly (index = rand_u32 mod count, in pool order) among keyframes with
+ * r_i > 0 and decrements it; when none is left, r_i = 2 for the d_k = max(1, floor(k/d))
+ * largest losses (ties to the lower index) and 1 for the rest.  A new keyframe's
+ * loss starts at +infinity.  create/destroy manage host memory only.
+ */
+typedef struct cgs_scheduler cgs_scheduler;
+cgs_scheduler *cgs_sched_create(int32_t d);
+void cgs_sched_destroy(cgs_scheduler *s);
+int cgs_sched_add(cgs_scheduler *s, int32_t keyframe_id, int32_t r0);  /* returns pool index */
+int cgs_sched_draw(cgs_scheduler *s, uint32_t rand_u32);             /* returns pool index */
+int cgs_sched_report(cgs_scheduler *s, int32_t index, double loss);
+/* copies keyframe ids, r and l of the first `cap` pool entries; returns the pool size */
+int cgs_sched_state(const cgs_scheduler *s, int32_t *ids, int32_t *r, double *l, int32_t cap);
+
+const char *cgs_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CGS_H */

@@ -767,3 +767,30 @@ int orc_densify_stats(const double *slot_grads, const int32_t *radius, int V, in
         }
     return 0;
 }
+
+/*
+ * Forward blend (Eq. 1) of a list of pixels only: pix[k] = (view, x, y); writes
+ * img[k][3] (with background), depth[k], T[k], last[k] and a near-threshold flag.
+ * For sampled comparisons on workloads too large to render in full.
+ */
+int orc_render_pixels(const double *rec, const uint32_t *ranges, const uint32_t *vals, int W, int H, int B,
+                      const double *bg, const int32_t *pix, int64_t npix, double tol, double *img, double *depth,
+                      double *Tfin, uint32_t *last, int32_t *near_px)
+{
+    int Tx = (W + B - 1) / B, Ty = (H + B - 1) / B;
+    for (int64_t k = 0; k < npix; k++) {
+        int v = pix[3 * k], x = pix[3 * k + 1], y = pix[3 * k + 2];
+        int64_t tile = (int64_t)v * Tx * Ty + (int64_t)(y / B) * Tx + (x / B);
+        uint32_t st = ranges[2 * tile], en = ranges[2 * tile + 1];
+        double C[3], D, T;
+        uint32_t lst;
+        int nr;
+        walk_pixel(rec, vals + st, (int64_t)en - st, (double)x, (double)y, tol, NULL, C, &D, &T, &lst, &nr, NULL);
+        for (int ch = 0; ch < 3; ch++) img[3 * k + ch] = C[ch] + T * bg[ch];
+        depth[k] = D;
+        Tfin[k] = T;
+        last[k] = lst;
+        near_px[k] = nr;
+    }
+    return 0;
+}

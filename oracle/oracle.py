@@ -64,6 +64,7 @@ def _load():
         lib.orc_preprocess_bwd.argtypes = [P, i64, i32, P, i32, i32, i32, i32, f64, P, P]
         lib.orc_densify_stats.argtypes = [P, P, i32, i64, i32, i32, P, P, P]
         lib.orc_sh_basis.argtypes = [i32, f64, f64, f64, P, P]
+        lib.orc_render_pixels.argtypes = [P, P, P, i32, i32, i32, P, P, i64, f64, P, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -147,6 +148,19 @@ def render_fwd(rec, ranges, vals, V, W, H, B, cams, bg=(0.0, 0.0, 0.0), tgt_rgb=
     del HW
     if want_hash:
         out["hash"] = int(h[0])
+    return out
+
+
+def render_pixels(rec, ranges, vals, W, H, B, pix, bg=(0.0, 0.0, 0.0), tol=0.0) -> dict:
+    """Forward blend of selected pixels only; pix is int[k][3] = (view, x, y)."""
+    lib = _load()
+    pix = np.ascontiguousarray(pix, np.int32)
+    k = pix.shape[0]
+    out = dict(img=np.zeros((k, 3)), depth=np.zeros(k), T=np.zeros(k), last=np.zeros(k, np.uint32),
+               near=np.zeros(k, np.int32))
+    lib.orc_render_pixels(_p(_f64(rec)), _p(np.ascontiguousarray(ranges, np.uint32)),
+                          _p(np.ascontiguousarray(vals, np.uint32)), W, H, B, _p(_f64(bg)), _p(pix), k, tol,
+                          _p(out["img"]), _p(out["depth"]), _p(out["T"]), _p(out["last"]), _p(out["near"]))
     return out
 
 

@@ -1,0 +1,307 @@
+// Tile binning of the window's projected splats (one shared sort for all views).
+//
+// The blending order of Eq. 1 (Sec. III-B, CaRtGS) is depth order within each
+// tile.  Instead of a global LSD radix sort over 64-bit (tile, depth) keys, which
+// reads and writes every instance once per digit pass, the sort here is
+// most-significant-digit first with the tile id as one full-width digit:
+//   1. k_count    : per-tile instance counts (atomic histogram over the rects)
+//   2. k_scan     : exclusive scan -> tile ranges (the digit's bucket offsets)
+//   3. k_scatter  : every instance is written once into its tile's bucket as the
+//                   64-bit key (depth bits << 32 | slot); the order inside a bucket
+//                   is arbitrary
+//   4. k_sort_*   : each bucket is sorted in shared memory.  The keys within a tile
+//                   are unique (a slot appears once per tile), so the result is one
+//                   well-defined order, (depth, slot) ascending, whatever order the
+//                   scatter produced.  Depth is positive, so its IEEE bits order
+//                   like its values.
+// Buckets longer than kSmallCap go to a second kernel with a larger shared-memory
+// buffer; buckets beyond that are sorted in place in global memory by one block.
+#include <algorithm>
+
+#include "cgs_internal.cuh"
+
+namespace cgs {
+
+constexpr int kSmallCap = 2048;      // keys per tile sorted by the 256-thread kernel
+constexpr int kSmallThreads = 256;
+constexpr int kBigThreads = 1024;
+constexpr int kBigCap = 16384;       // keys held in shared memory by the big-tile kernel
+constexpr uint64_t kPadKey = ~0ull;  // larger than any real key
+
+struct BinWs {
+    uint32_t *count;     // [Ttot + 1]
+    uint32_t *cursor;    // [Ttot]
+    uint32_t *nbig;      // [1]
+    uint32_t *big;       // [Ttot]
+    uint64_t *keys;      // [capacity]
+};
+
+static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Sections: counters (one memset), big-tile list, keys.
+static size_t ws_layout(int64_t capacity, int64_t Ttot, BinWs *w, void *base)
+{
+    size_t head = align256(sizeof(uint32_t) * (2 * (size_t)Ttot + 2));
+    size_t bigb = align256(sizeof(uint32_t) * (size_t)Ttot);
+    size_t keyb = align256(sizeof(uint64_t) * (size_t)(capacity > 0 ? capacity : 1));
+    if (w && base) {
+        char *b = static_cast<char *>(base);
+        w->count = reinterpret_cast<uint32_t *>(b);
+        w->cursor = w->count + Ttot + 1;
+        w->nbig = w->cursor + Ttot;
+        w->big = reinterpret_cast<uint32_t *>(b + head);
+        w->keys = reinterpret_cast<uint64_t *>(b + head + bigb);
+    }
+    return head + bigb + keyb;
+}
+
+size_t bin_ws_bytes(int64_t capacity, int64_t Ttot) { return ws_layout(capacity, Ttot, nullptr, nullptr); }
+
+__device__ __forceinline__ bool load_slot(const float4 *__restrict__ rec, int64_t slot, float &u, float &v,
+                                          float &z, int &r)
+{
+    const float *rf = reinterpret_cast<const float *>(rec + kRec4 * slot);
+    r = __float_as_int(__ldg(rf + 7));
+    if (r <= 0) return false;
+    float4 a = __ldg(rec + kRec4 * slot);
+    u = a.x;
+    v = a.y;
+    z = __ldg(rf + 6);
+    return true;
+}
+
+__global__ void k_count(const float4 *__restrict__ rec, int64_t n, int V, Grid g, uint32_t *__restrict__ count)
+{
+    const int64_t total = (int64_t)V * n;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total; s += (int64_t)gridDim.x * blockDim.x) {
+        float u, v, z;
+        int r;
+        if (!load_slot(rec, s, u, v, z, r)) continue;
+        const int64_t view = s / n;
+        Rect R = tile_rect(u, v, r, g);
+        uint32_t *base = count + view * g.Tv;
+        for (int ty = R.y0; ty < R.y1; ty++)
+            for (int tx = R.x0; tx < R.x1; tx++) atomicAdd(base + ty * g.Tx + tx, 1u);
+    }
+}
+
+// Single-block exclusive scan of the per-tile counts; writes ranges (clamped to the
+// capacity), the total instance count and the capacity status.
+__global__ void __launch_bounds__(1024)
+k_scan(uint32_t *__restrict__ count, int64_t Ttot, int64_t capacity, uint32_t *__restrict__ ranges,
+       int64_t *__restrict__ n_inst, int32_t *__restrict__ status)
+{
+    __shared__ unsigned long long part[1024];
+    const int64_t per = (Ttot + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = threadIdx.x * per, hi = min(Ttot, lo + per);
+    unsigned long long s = 0;
+    for (int64_t t = lo; t < hi; t++) s += count[t];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    // Hillis-Steele inclusive scan of the 1024 partial sums
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        unsigned long long x = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
+        __syncthreads();
+        part[threadIdx.x] += x;
+        __syncthreads();
+    }
+    unsigned long long run = threadIdx.x ? part[threadIdx.x - 1] : 0ull;
+    const unsigned long long cap = (unsigned long long)capacity;
+    for (int64_t t = lo; t < hi; t++) {
+        unsigned long long c = count[t];
+        unsigned long long st = run, en = run + c;
+        count[t] = (uint32_t)min(st, cap);      // bucket start (clamped) for the scatter
+        ranges[2 * t] = (uint32_t)min(st, cap);
+        ranges[2 * t + 1] = (uint32_t)min(en, cap);
+        run = en;
+    }
+    if (threadIdx.x == blockDim.x - 1) {
+        unsigned long long total = part[blockDim.x - 1];
+        *n_inst = (int64_t)total;
+        count[Ttot] = (uint32_t)min(total, cap);
+        if (total > cap) set_status(status, CGS_ERR_CAPACITY);
+    }
+}
+
+__global__ void k_scatter(const float4 *__restrict__ rec, int64_t n, int V, Grid g,
+                          const uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
+                          uint64_t *__restrict__ keys, int64_t capacity)
+{
+    const int64_t total = (int64_t)V * n;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total; s += (int64_t)gridDim.x * blockDim.x) {
+        float u, v, z;
+        int r;
+        if (!load_slot(rec, s, u, v, z, r)) continue;
+        const int64_t view = s / n;
+        Rect R = tile_rect(u, v, r, g);
+        const uint64_t key = ((uint64_t)__float_as_uint(z) << 32) | (uint64_t)(uint32_t)s;
+        for (int ty = R.y0; ty < R.y1; ty++)
+            for (int tx = R.x0; tx < R.x1; tx++) {
+                const int64_t t = view * g.Tv + ty * g.Tx + tx;
+                const uint64_t pos = (uint64_t)start[t] + atomicAdd(cursor + t, 1u);
+                if (pos < (uint64_t)capacity) keys[pos] = key;
+            }
+    }
+}
+
+// Compare-exchange network of an ascending bitonic sort in which every comparator
+// puts the smaller key at the lower index (the first stage of each merge compares
+// mirrored pairs), so padding with the largest key at the end is never moved.
+__device__ __forceinline__ void bitonic_pair(uint32_t i, uint32_t k, uint32_t d, bool flip, uint32_t &a, uint32_t &b)
+{
+    if (flip) {
+        const uint32_t half = k >> 1, blk = i / half, off = i % half;
+        a = blk * k + off;
+        b = blk * k + k - 1 - off;
+    } else {
+        const uint32_t blk = i / d, off = i % d;
+        a = blk * 2 * d + off;
+        b = a + d;
+    }
+}
+
+__device__ __forceinline__ void smem_bitonic(uint64_t *s, uint32_t P)
+{
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t d = k >> 1; d >= 1; d >>= 1) {
+            const bool flip = (d == (k >> 1));
+            for (uint32_t i = threadIdx.x; i < P / 2; i += blockDim.x) {
+                uint32_t a, b;
+                bitonic_pair(i, k, d, flip, a, b);
+                uint64_t x = s[a], y = s[b];
+                if (y < x) {
+                    s[a] = y;
+                    s[b] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t next_pow2(uint32_t x)
+{
+    return x <= 1 ? 1u : 1u << (32 - __clz(x - 1));
+}
+
+__global__ void __launch_bounds__(kSmallThreads)
+k_sort_small(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+             uint32_t *__restrict__ big, uint32_t *__restrict__ nbig)
+{
+    __shared__ uint64_t s[kSmallCap];
+    const int64_t t = blockIdx.x;
+    const uint32_t st = ranges[2 * t], en = ranges[2 * t + 1];
+    const uint32_t len = en - st;
+    if (len == 0) return;
+    if (len > kSmallCap) {
+        if (threadIdx.x == 0) big[atomicAdd(nbig, 1u)] = (uint32_t)t;
+        return;
+    }
+    if (len == 1) {
+        if (threadIdx.x == 0) vals[st] = (uint32_t)keys[st];
+        return;
+    }
+    const uint32_t P = next_pow2(len);
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < len ? keys[st + i] : kPadKey;
+    __syncthreads();
+    smem_bitonic(s, P);
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) vals[st + i] = (uint32_t)s[i];
+}
+
+__global__ void __launch_bounds__(kBigThreads)
+k_sort_big(const uint32_t *__restrict__ ranges, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+           const uint32_t *__restrict__ big, const uint32_t *__restrict__ nbig)
+{
+    extern __shared__ uint64_t sbig[];
+    const uint32_t nb = *nbig;
+    for (uint32_t bi = blockIdx.x; bi < nb; bi += gridDim.x) {
+        const uint32_t t = big[bi];
+        const uint32_t st = ranges[2 * t], en = ranges[2 * t + 1];
+        const uint32_t len = en - st;
+        const uint32_t P = next_pow2(len);
+        if (len <= (uint32_t)kBigCap) {
+            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) sbig[i] = i < len ? keys[st + i] : kPadKey;
+            __syncthreads();
+            smem_bitonic(sbig, P);
+            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) vals[st + i] = (uint32_t)sbig[i];
+        } else {
+            // in place in global memory; comparators reaching past the list compare
+            // against the implicit padding and leave both sides unchanged
+            uint64_t *k0 = keys + st;
+            for (uint32_t k = 2; k <= P; k <<= 1) {
+                for (uint32_t d = k >> 1; d >= 1; d >>= 1) {
+                    const bool flip = (d == (k >> 1));
+                    for (uint32_t i = threadIdx.x; i < P / 2; i += blockDim.x) {
+                        uint32_t a, b;
+                        bitonic_pair(i, k, d, flip, a, b);
+                        if (b >= len) continue;
+                        uint64_t x = k0[a], y = k0[b];
+                        if (y < x) {
+                            k0[a] = y;
+                            k0[b] = x;
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) vals[st + i] = (uint32_t)k0[i];
+        }
+        __syncthreads();
+    }
+}
+
+// Work order for the raster kernels: tiles by decreasing list length (bucketed by
+// floor(log2(len)), longest bucket first; tile order inside a bucket is arbitrary).
+__global__ void __launch_bounds__(1024)
+k_tile_order(const uint32_t *__restrict__ ranges, int64_t Ttot, uint32_t *__restrict__ order)
+{
+    __shared__ uint32_t hist[33], offs[33];
+    if (threadIdx.x < 33) hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < Ttot; t += blockDim.x) {
+        uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
+        uint32_t b = len ? 32 - __clz(len) : 0;     // 0 for empty, 1..32 otherwise
+        atomicAdd(&hist[b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 32; b >= 0; b--) {
+            offs[b] = run;
+            run += hist[b];
+        }
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < Ttot; t += blockDim.x) {
+        uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
+        uint32_t b = len ? 32 - __clz(len) : 0;
+        order[atomicAdd(&offs[b], 1u)] = (uint32_t)t;
+    }
+}
+
+cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws, int64_t capacity,
+                     uint32_t *vals, uint32_t *ranges, uint32_t *order, int64_t *n_inst, int32_t *status,
+                     int num_sms, cudaStream_t s)
+{
+    const int64_t Ttot = g.Tv * V;
+    BinWs w;
+    ws_layout(capacity, Ttot, &w, ws);
+    const float4 *r4 = reinterpret_cast<const float4 *>(rec);
+    cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (2 * (size_t)Ttot + 2), s);
+    if (e != cudaSuccess) return e;
+    const int64_t slots = (int64_t)V * n;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((slots + threads - 1) / threads, (int64_t)num_sms * 16);
+    k_count<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count);
+    k_scan<<<1, 1024, 0, s>>>(w.count, Ttot, capacity, ranges, n_inst, status);
+    k_scatter<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count, w.cursor, w.keys, capacity);
+    k_sort_small<<<(unsigned)Ttot, kSmallThreads, 0, s>>>(ranges, w.keys, vals, w.big, w.nbig);
+    const size_t big_smem = sizeof(uint64_t) * kBigCap;
+    e = cudaFuncSetAttribute(k_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem);
+    if (e != cudaSuccess) return e;
+    k_sort_big<<<num_sms, kBigThreads, big_smem, s>>>(ranges, w.keys, vals, w.big, w.nbig);
+    if (order) k_tile_order<<<1, 1024, 0, s>>>(ranges, Ttot, order);
+    return cudaGetLastError();
+}
+
+}  // namespace cgs

@@ -1,0 +1,244 @@
+"""One CaRtGS mapping iteration over a window of keyframes, on the GPU.
+
+`MappingWindow` owns the device-resident state of the photorealistic mapping
+back-end (Sec. III-B): the Gaussian parameters, their Adam moments, the
+densification statistics, and every buffer the iteration writes.  One window
+iteration is preprocess -> bin_sort -> render_fwd (+ L1 loss) -> render_bwd
+(+ densify statistics) -> Adam, each step a libcgs call.  PyTorch only allocates
+memory and supplies the stream.
+
+Two forms of the same iteration:
+  * batched  (`step`): every view of the window in one launch per stage, the
+    parameters read once per window, one shared tile sort;
+  * per-view (`step_per_view`): the same math one view at a time (V launches of
+    each raster stage), gradients accumulated, one Adam step.
+Both give the same gradients (up to float summation order).
+
+`capture()` records one batched iteration into a CUDA graph; `replay()` runs it.
+The Adam step counter lives on the device, so replays advance it.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import _native as N
+
+# Per-group learning rates: means, log_scales, quats, opacity, sh_dc, sh_rest.
+LR_DEFAULT = (1.6e-4, 5e-3, 1e-3, 2.5e-2, 2.5e-3, 2.5e-3 / 20.0)
+
+
+def _u32(n, device):
+    """uint32 storage (torch has no general uint32 arithmetic; int32 holds the bits)."""
+    return torch.empty(n, dtype=torch.int32, device=device)
+
+
+class MappingWindow:
+    def __init__(self, params: torch.Tensor, n: int, sh_degree: int, width: int, height: int, views: int,
+                 tile: int = 16, batch_depth: int = 64, lr=LR_DEFAULT, lambda_o: float = 0.0,
+                 lambda_depth: float = 0.1, bg=(0.0, 0.0, 0.0), near_z: float = 0.2,
+                 betas=(0.9, 0.999), eps: float = 1e-15, capacity: int | None = None,
+                 densify_stats: bool = True, tile_order: bool = True):
+        if not params.is_cuda or params.dtype != torch.float32:
+            raise ValueError("params must be a float32 CUDA tensor")
+        dev = params.device
+        self.device = dev
+        self.n, self.V, self.sh_degree = int(n), int(views), int(sh_degree)
+        self.W, self.H = int(width), int(height)
+        self.cfg = N.make_config(width, height, tile, batch_depth, sh_degree, near_z, bg, lambda_depth)
+        P = N.cgs_param_count(n, sh_degree)
+        if params.numel() != P:
+            raise ValueError(f"params has {params.numel()} floats, expected {P}")
+        self.P = P
+        self.lr = tuple(float(x) for x in lr)
+        self.lambda_o = float(lambda_o)
+        self.betas = (float(betas[0]), float(betas[1]))
+        self.eps = float(eps)
+        self.densify = densify_stats
+        f32 = dict(dtype=torch.float32, device=dev)
+
+        self.params = params.contiguous()
+        self.grads = torch.zeros(P, **f32)
+        self.m = torch.zeros(P, **f32)
+        self.v = torch.zeros(P, **f32)
+        self.step_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+
+        V, H, W = self.V, self.H, self.W
+        self.cams = torch.zeros(V, N.CAM_FLOATS, **f32)
+        self.view_weight = torch.ones(V, **f32)
+        self.tgt_rgb = torch.zeros(V, 3, H, W, **f32)
+        self.tgt_depth = torch.zeros(V, H, W, **f32)
+
+        slots = V * self.n
+        self.rec = torch.zeros(slots * N.REC_FLOATS, **f32)
+        self.slot_grad = torch.zeros(slots * N.REC_FLOATS, **f32)
+        self.Tv = N.cgs_tiles_per_view(self.cfg)
+        self.Ttot = self.Tv * V
+        self.ranges = _u32(2 * self.Ttot, dev)
+        self.order = _u32(self.Ttot, dev) if tile_order else None
+        self.n_inst = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+        self.img = torch.zeros(V, 3, H, W, **f32)
+        self.depth = torch.zeros(V, H, W, **f32)
+        self.t_final = torch.zeros(V, H, W, **f32)
+        self.last = torch.zeros(V, H, W, dtype=torch.int32, device=dev)
+        self.loss_view = torch.zeros(V, **f32)
+        self.depth_count = torch.zeros(V, dtype=torch.int32, device=dev)
+        self.loss_o = torch.zeros(1, **f32)
+        self.fwd_ws = torch.empty(max(256, N.cgs_render_fwd_workspace(V, self.cfg)), dtype=torch.uint8,
+                                  device=dev)
+        self.accum = torch.zeros(self.n, **f32)
+        self.denom = torch.zeros(self.n, **f32)
+        self.max_r2d = torch.zeros(self.n, **f32)
+        self._pv = None
+        self.graph = None
+        self._alloc_capacity(capacity if capacity else max(1 << 20, 16 * slots))
+
+    # ------------------------------------------------------------ buffers
+    def _alloc_capacity(self, cap: int):
+        self.capacity = int(cap)
+        self.vals = _u32(max(1, self.capacity), self.device)
+        ws = N.cgs_bin_sort_workspace(self.capacity, self.V, self.cfg)
+        self.bin_ws = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        self._pv = None
+        self.graph = None
+
+    def set_window(self, cams, tgt_rgb, tgt_depth=None, view_weight=None, non_blocking=True):
+        """Copy the window's cameras (float32[V][20]), targets and view weights into the
+        resident buffers (host tensors should be pinned for an asynchronous copy)."""
+        self.cams.copy_(torch.as_tensor(cams).reshape(self.V, N.CAM_FLOATS), non_blocking=non_blocking)
+        self.tgt_rgb.copy_(torch.as_tensor(tgt_rgb).reshape(self.tgt_rgb.shape), non_blocking=non_blocking)
+        if tgt_depth is not None:
+            self.tgt_depth.copy_(torch.as_tensor(tgt_depth).reshape(self.tgt_depth.shape),
+                                 non_blocking=non_blocking)
+        else:
+            self.tgt_depth.zero_()
+        if view_weight is not None:
+            self.view_weight.copy_(torch.as_tensor(view_weight, dtype=torch.float32), non_blocking=non_blocking)
+
+    # ---------------------------------------------------------- iteration
+    def forward(self, with_loss: bool = True, params: torch.Tensor | None = None):
+        """Preprocess, bin and render every view of the window (loss fused if with_loss).
+        `params` overrides the window's own parameter vector (same layout)."""
+        c = self.cfg
+        p = self.params if params is None else params
+        N.cgs_preprocess(p, self.n, self.cams, self.V, c, self.rec, self.slot_grad, self.status)
+        N.cgs_bin_sort(self.rec, self.n, self.V, c, self.bin_ws, self.capacity, self.vals, self.ranges,
+                       self.order, self.n_inst, self.status)
+        N.cgs_render_fwd(self.rec, self.vals, self.ranges, self.order, self.V, c, self.view_weight,
+                         self.tgt_rgb if with_loss else None, self.tgt_depth if with_loss else None,
+                         self.img, self.depth, self.t_final, self.last, self.loss_view, self.depth_count,
+                         self.fwd_ws, self.status)
+
+    def backward(self, dl_dimg=None, dl_ddepth=None, params: torch.Tensor | None = None,
+                 grads_out: torch.Tensor | None = None):
+        """Raster backward + chain rule to the parameters; overwrites self.grads (or
+        grads_out).  Pixel gradients come from the fused L1 loss unless dl_dimg is given."""
+        d = self.densify and dl_dimg is None
+        p = self.params if params is None else params
+        g = self.grads if grads_out is None else grads_out
+        N.cgs_render_bwd(p, self.n, self.cams, self.V, self.cfg, self.rec, self.vals, self.ranges,
+                         self.order, self.view_weight, self.img, self.depth, self.t_final, self.last,
+                         self.tgt_rgb, self.tgt_depth, self.depth_count, dl_dimg, dl_ddepth, self.slot_grad,
+                         g, False, self.accum if d else None, self.denom if d else None,
+                         self.max_r2d if d else None, self.status)
+
+    def optimizer_step(self):
+        N.cgs_adam(self.params, self.grads, self.m, self.v, self.n, self.sh_degree, self.lr, self.betas[0],
+                   self.betas[1], self.eps, 0, self.lambda_o, self.loss_o, step_dev=self.step_dev)
+
+    def step(self):
+        """One batched window iteration: fwd + loss + bwd + densify stats + Adam."""
+        self.forward()
+        self.backward()
+        self.optimizer_step()
+
+    # ------------------------------------------------------- per-view form
+    def _per_view_buffers(self):
+        if self._pv is None:
+            dev, n = self.device, self.n
+            pv = {}
+            pv["rec"] = torch.zeros(n * N.REC_FLOATS, dtype=torch.float32, device=dev)
+            pv["slot_grad"] = torch.zeros(n * N.REC_FLOATS, dtype=torch.float32, device=dev)
+            pv["ranges"] = _u32(2 * self.Tv, dev)
+            pv["order"] = _u32(self.Tv, dev) if self.order is not None else None
+            pv["ws"] = torch.empty(N.cgs_bin_sort_workspace(self.capacity, 1, self.cfg), dtype=torch.uint8,
+                                   device=dev)
+            pv["fwd_ws"] = torch.empty(max(256, N.cgs_render_fwd_workspace(1, self.cfg)), dtype=torch.uint8,
+                                       device=dev)
+            self._pv = pv
+        return self._pv
+
+    def step_per_view(self):
+        """The same iteration, one view at a time (gradients accumulated, one Adam step)."""
+        pv = self._per_view_buffers()
+        c = self.cfg
+        d = self.densify
+        for v in range(self.V):
+            cam = self.cams[v:v + 1]
+            N.cgs_preprocess(self.params, self.n, cam, 1, c, pv["rec"], pv["slot_grad"], self.status)
+            N.cgs_bin_sort(pv["rec"], self.n, 1, c, pv["ws"], self.capacity, self.vals, pv["ranges"], pv["order"],
+                           self.n_inst, self.status)
+            img, dep, tf, la = self.img[v:v + 1], self.depth[v:v + 1], self.t_final[v:v + 1], self.last[v:v + 1]
+            tr, td = self.tgt_rgb[v:v + 1], self.tgt_depth[v:v + 1]
+            w, lv, dc = self.view_weight[v:v + 1], self.loss_view[v:v + 1], self.depth_count[v:v + 1]
+            N.cgs_render_fwd(pv["rec"], self.vals, pv["ranges"], pv["order"], 1, c, w, tr, td, img, dep, tf, la,
+                             lv, dc, pv["fwd_ws"], self.status)
+            N.cgs_render_bwd(self.params, self.n, cam, 1, c, pv["rec"], self.vals, pv["ranges"], pv["order"], w,
+                             img, dep, tf, la, tr, td, dc, None, None, pv["slot_grad"], self.grads, v > 0,
+                             self.accum if d else None, self.denom if d else None, self.max_r2d if d else None,
+                             self.status)
+        self.optimizer_step()
+
+    # --------------------------------------------------------- CUDA graph
+    def capture(self, warmup: int = 0):
+        """Record one batched iteration (`step`) into a CUDA graph."""
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self.step()
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step()
+        self.graph = g
+        return g
+
+    def replay(self):
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        self.graph.replay()
+
+    # ------------------------------------------------------------- status
+    def read_status(self) -> tuple[int, int]:
+        """(device status, instance count) -- synchronises."""
+        return int(self.status.item()), int(self.n_inst.item())
+
+    def ensure_capacity(self, headroom: float = 1.25) -> bool:
+        """Check the device status after an iteration; on a capacity overflow, grow the
+        instance buffers (dropping any captured graph) and return False so the caller
+        re-runs the iteration."""
+        st, ninst = self.read_status()
+        if st == N.CGS_ERR_CAPACITY:
+            self.status.zero_()
+            self._alloc_capacity(int(math.ceil(ninst * headroom)))
+            return False
+        if st != 0:
+            raise N.CgsError("device status", st)
+        return True
+
+    def fit_capacity(self, headroom: float = 1.25):
+        """Run the forward once and size the instance buffers to headroom x the count."""
+        self.forward(with_loss=False)
+        ok = self.ensure_capacity(headroom)
+        if not ok:
+            self.forward(with_loss=False)
+            self.ensure_capacity(headroom)
+        ninst = int(self.n_inst.item())
+        want = int(math.ceil(max(ninst, 1) * headroom))
+        if want < self.capacity // 2 or want > self.capacity:
+            self._alloc_capacity(want)
+        return ninst

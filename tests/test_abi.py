@@ -1,0 +1,89 @@
+"""The C-ABI library builds, loads, exports every symbol include/cgs.h declares, and
+rejects bad arguments before touching a GPU (CPU only: no compute call runs)."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+HEADER = ROOT / "include" / "cgs.h"
+
+
+def declared_functions():
+    text = re.sub(r"/\*.*?\*/", "", HEADER.read_text(), flags=re.S)
+    return sorted(set(re.findall(r"\b(cgs_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_2410_00486_gb300 import build as B
+    B.build()
+    from paper_2410_00486_gb300 import _native as N
+    N.lib()
+    return N
+
+
+def test_every_declared_symbol_is_exported(native):
+    names = declared_functions()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(str(native.LIB_PATH))
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(native.EXPORTS) == set(names)
+
+
+def test_struct_sizes_match_header(native):
+    assert ctypes.sizeof(native.cgs_camera) == 80
+    assert ctypes.sizeof(native.cgs_config) == 4 * 10
+
+
+def test_host_only_queries(native):
+    cfg = native.make_config(1200, 680, 16, 64, 3)
+    assert native.cgs_param_count(300_000, 3) == 59 * 300_000
+    assert native.cgs_param_count(10, 0) == 140
+    assert native.cgs_tiles_per_view(cfg) == 75 * 43
+    assert native.cgs_bin_sort_workspace(1000, 16, cfg) > 16 * 75 * 43 * 8
+    bad = native.make_config(1200, 680, 12, 64, 3)
+    assert native.cgs_tiles_per_view(bad) == -1
+    assert native.status_string(-4).startswith("tile instance capacity")
+
+
+def test_argument_validation_needs_no_gpu(native):
+    L = native.lib()
+    cfg = native.make_config(64, 48, 16, 64, 1)
+    # null pointers / bad sizes / bad options are refused before any CUDA call
+    assert L.cgs_preprocess(None, 10, None, 1, ctypes.byref(cfg), None, None, None, None) == native.CGS_ERR_ARG
+    bad = native.make_config(64, 48, 16, 48, 1)
+    assert L.cgs_preprocess(8, 10, 16, 1, ctypes.byref(bad), 16, None, None, None) == native.CGS_ERR_ARG
+    assert L.cgs_preprocess(8, 0, 16, 1, ctypes.byref(cfg), 16, None, None, None) == native.CGS_ERR_ARG
+    assert L.cgs_preprocess(8, 10, 16, 1, ctypes.byref(cfg), 8, None, None, None) == native.CGS_ERR_ARG  # unaligned
+    assert L.cgs_bin_sort(16, 10, 1, ctypes.byref(cfg), 256, 0, 100, 16, 16, None, 16, None, None) == \
+        native.CGS_ERR_WORKSPACE
+    assert L.cgs_adam(None, None, None, None, 10, 1, None, 0.9, 0.999, 1e-15, 1, None, 0.0, None, None) == \
+        native.CGS_ERR_ARG
+    lr = (ctypes.c_float * 6)()
+    assert L.cgs_adam(16, 16, 16, 16, 10, 1, ctypes.cast(lr, ctypes.c_void_p), 0.9, 0.999, 1e-15, 0, None,
+                      0.0, None, None) == native.CGS_ERR_ARG   # step < 1 without a device counter
+
+
+def test_scheduler_matches_oracle(native):
+    """The library's host scheduler draws exactly like the oracle's (Eqs. 5-8)."""
+    import numpy as np
+    from oracle import oracle as O
+    rng = np.random.default_rng(0)
+    lib_s, orc_s = native.Scheduler(4), O.Scheduler(4)
+    for step in range(400):
+        if step % 23 == 0:
+            k = len(orc_s.K)
+            r0 = 8 if k % 2 else 2
+            assert lib_s.add(k, r0) == k
+            orc_s.add(k, r0)
+        u = int(rng.integers(0, 2 ** 32))
+        a, b = lib_s.draw(u), orc_s.draw(u)
+        assert a == b
+        loss = float(rng.uniform(0, 1)) if rng.uniform() > 0.1 else 0.5
+        lib_s.report(a, loss)
+        orc_s.report(b, loss)
+        ids, r, l = lib_s.state()
+        assert r == orc_s.R

@@ -184,3 +184,17 @@ def test_l1_loss_closed_form():
         exp = np.abs(d_img[v]).mean() + 0.1 * np.abs(fw0["depth"][v][m] - tgt_d[v][m]).mean()
         assert fw["loss_view"][v] == pytest.approx(exp, rel=1e-12)
         assert fw["depth_count"][v] == m.sum()
+
+
+def test_render_pixels_matches_full_render():
+    sc = make_scene(1, n=500)
+    pre = O.preprocess(sc.params, sc.n, 0, sc.cams, 160, 120, 16)
+    rec = pre["rec"]
+    ranges, vals = O.bin_lists(rec[:, 0], rec[:, 1], rec[:, 9], pre["radius"], 1, sc.n, 160, 120, 16)
+    fw = O.render_fwd(rec, ranges, vals, 1, 160, 120, 16, sc.cams, bg=(0.1, 0.2, 0.3))
+    rng = np.random.default_rng(0)
+    pix = np.stack([np.zeros(50, int), rng.integers(0, 160, 50), rng.integers(0, 120, 50)], 1)
+    px = O.render_pixels(rec, ranges, vals, 160, 120, 16, pix, bg=(0.1, 0.2, 0.3))
+    np.testing.assert_array_equal(px["img"], fw["img"][0][:, pix[:, 2], pix[:, 1]].T)
+    np.testing.assert_array_equal(px["T"], fw["T"][0][pix[:, 2], pix[:, 1]])
+    np.testing.assert_array_equal(px["last"], fw["last"][0][pix[:, 2], pix[:, 1]])
