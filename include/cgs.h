@@ -129,7 +129,8 @@ int cgs_preprocess(const float *params, int64_t n, const cgs_camera *cams, int32
  *              256-byte aligned
  *   capacity   number of entries `vals` can hold
  *   vals       device out, uint32[capacity]: slot ids, tile after tile
- *   ranges     device out, uint32[2 * V * tiles_per_view]: [start, end) of each tile
+ *   ranges     device out, uint32[2 * V * tiles_per_view]: [start, end) of each tile, the
+ *              exclusive scan of the per-tile counts (an empty tile is [start, start))
  *   tile_order device out (may be NULL), uint32[V * tiles_per_view]: tiles ordered
  *              by decreasing list length (work order for the raster kernels)
  *   n_inst_dev device out, int64: total number of tile instances (also when it

@@ -354,7 +354,8 @@ static int inst_cmp(const void *pa, const void *pb)
  * slot = v*n + g, so equal depths keep the Gaussian order (reading).  Depth
  * order is the blending order of Eq. 1.  Inputs are the projected centre, radius
  * and depth of each slot (radius 0 = culled).  Outputs: ranges[2*Ttot] = [start,
- * end) per global tile, vals[count] = slot ids.  Returns the instance count; writes
+ * end) per global tile, the exclusive scan of the per-tile counts (an empty tile
+ * is [start, start)), vals[count] = slot ids.  Returns the instance count; writes
  * nothing when that count exceeds `capacity` or vals is NULL (a sizing call).
  */
 int64_t orc_bin(const double *u, const double *v, const double *z, const int32_t *radius,
@@ -387,12 +388,15 @@ int64_t orc_bin(const double *u, const double *v, const double *z, const int32_t
                 }
         }
     qsort(ins, count, sizeof(inst_t), inst_cmp);
-    for (int64_t t = 0; t < Ttot; t++) { ranges[2 * t] = 0; ranges[2 * t + 1] = 0; }
-    for (int64_t i = 0; i < count; i++) {
-        vals[i] = (uint32_t)ins[i].slot;
-        int64_t t = ins[i].tile;
-        if (i == 0 || ins[i - 1].tile != t) ranges[2 * t] = (uint32_t)i;
-        ranges[2 * t + 1] = (uint32_t)(i + 1);
+    /* ranges: exclusive scan of the per-tile counts (an empty tile is [pos, pos)) */
+    int64_t i = 0;
+    for (int64_t t = 0; t < Ttot; t++) {
+        ranges[2 * t] = (uint32_t)i;
+        while (i < count && ins[i].tile == t) {
+            vals[i] = (uint32_t)ins[i].slot;
+            i++;
+        }
+        ranges[2 * t + 1] = (uint32_t)i;
     }
     free(ins);
     return count;

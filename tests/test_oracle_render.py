@@ -160,10 +160,9 @@ def test_bin_lists_brute_force(seed):
     for t in range(V * Tx * Ty):
         st, en = ranges[t]
         lst = sorted(expect.get(t, []), key=lambda s: (float(z[s]), s))
-        if lst:
-            assert st == pos
+        assert st == pos                     # ranges are the exclusive scan of the counts
         assert list(vals[st:en]) == lst
-        pos = en if lst else pos
+        pos = en
     assert pos == len(vals)
 
 
