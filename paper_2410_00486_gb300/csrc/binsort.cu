@@ -27,6 +27,7 @@ constexpr int kSmallThreads = 256;
 constexpr int kBigThreads = 1024;
 constexpr int kBigCap = 16384;       // keys held in shared memory by the big-tile kernel
 constexpr uint64_t kPadKey = ~0ull;  // larger than any real key
+constexpr size_t kAggMaxSmem = 96 * 1024;   // per-view tile histogram in shared memory
 
 struct BinWs {
     uint32_t *count;     // [Ttot + 1]
@@ -83,6 +84,35 @@ __global__ void k_count(const float4 *__restrict__ rec, int64_t n, int V, Grid g
         for (int ty = R.y0; ty < R.y1; ty++)
             for (int tx = R.x0; tx < R.x1; tx++) atomicAdd(base + ty * g.Tx + tx, 1u);
     }
+}
+
+// Shared-memory aggregated variants, used when a view's tile histogram fits in shared
+// memory: block (c, v) owns slots [c*kChunk, (c+1)*kChunk) of view v, counts its
+// instances per tile in shared memory and touches each global counter once.
+constexpr int kChunk = 4096;
+constexpr int kAggThreads = 512;
+
+__global__ void __launch_bounds__(kAggThreads)
+k_count_agg(const float4 *__restrict__ rec, int64_t n, Grid g, uint32_t *__restrict__ count)
+{
+    extern __shared__ uint32_t hist[];
+    const int view = blockIdx.y;
+    const int64_t s0 = (int64_t)blockIdx.x * kChunk;
+    const int64_t s1 = min(n, s0 + kChunk);
+    for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    for (int64_t gi = s0 + threadIdx.x; gi < s1; gi += blockDim.x) {
+        float u, v, z;
+        int r;
+        if (!load_slot(rec, (int64_t)view * n + gi, u, v, z, r)) continue;
+        Rect R = tile_rect(u, v, r, g);
+        for (int ty = R.y0; ty < R.y1; ty++)
+            for (int tx = R.x0; tx < R.x1; tx++) atomicAdd(&hist[ty * g.Tx + tx], 1u);
+    }
+    __syncthreads();
+    uint32_t *base = count + (int64_t)view * g.Tv;
+    for (int t = threadIdx.x; t < g.Tv; t += blockDim.x)
+        if (hist[t]) atomicAdd(base + t, hist[t]);
 }
 
 // Single-block exclusive scan of the per-tile counts; writes ranges (clamped to the
@@ -144,31 +174,78 @@ __global__ void k_scatter(const float4 *__restrict__ rec, int64_t n, int V, Grid
     }
 }
 
+// Aggregated scatter (same block decomposition as k_count_agg): the block counts its
+// instances per tile again, reserves one contiguous run per tile in each bucket with a
+// single global atomic, then places its instances with shared-memory atomics.
+__global__ void __launch_bounds__(kAggThreads)
+k_scatter_agg(const float4 *__restrict__ rec, int64_t n, Grid g, const uint32_t *__restrict__ start,
+              uint32_t *__restrict__ cursor, uint64_t *__restrict__ keys, int64_t capacity)
+{
+    extern __shared__ uint32_t hist[];     // [Tv] counts, then run positions
+    const int view = blockIdx.y;
+    const int64_t s0 = (int64_t)blockIdx.x * kChunk;
+    const int64_t s1 = min(n, s0 + kChunk);
+    for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    for (int64_t gi = s0 + threadIdx.x; gi < s1; gi += blockDim.x) {
+        float u, v, z;
+        int r;
+        if (!load_slot(rec, (int64_t)view * n + gi, u, v, z, r)) continue;
+        Rect R = tile_rect(u, v, r, g);
+        for (int ty = R.y0; ty < R.y1; ty++)
+            for (int tx = R.x0; tx < R.x1; tx++) atomicAdd(&hist[ty * g.Tx + tx], 1u);
+    }
+    __syncthreads();
+    const int64_t tbase = (int64_t)view * g.Tv;
+    for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) {
+        const uint32_t c = hist[t];
+        if (c) hist[t] = start[tbase + t] + atomicAdd(cursor + tbase + t, c);
+    }
+    __syncthreads();
+    for (int64_t gi = s0 + threadIdx.x; gi < s1; gi += blockDim.x) {
+        const int64_t s = (int64_t)view * n + gi;
+        float u, v, z;
+        int r;
+        if (!load_slot(rec, s, u, v, z, r)) continue;
+        Rect R = tile_rect(u, v, r, g);
+        const uint64_t key = ((uint64_t)__float_as_uint(z) << 32) | (uint64_t)(uint32_t)s;
+        for (int ty = R.y0; ty < R.y1; ty++)
+            for (int tx = R.x0; tx < R.x1; tx++) {
+                const uint64_t pos = atomicAdd(&hist[ty * g.Tx + tx], 1u);
+                if (pos < (uint64_t)capacity) keys[pos] = key;
+            }
+    }
+}
+
 // Compare-exchange network of an ascending bitonic sort in which every comparator
 // puts the smaller key at the lower index (the first stage of each merge compares
 // mirrored pairs), so padding with the largest key at the end is never moved.
-__device__ __forceinline__ void bitonic_pair(uint32_t i, uint32_t k, uint32_t d, bool flip, uint32_t &a, uint32_t &b)
+// k (merge size) and d (comparator distance) are powers of two: index arithmetic is
+// shifts and masks (lk = log2 k, ld = log2 d).
+__device__ __forceinline__ void bitonic_pair(uint32_t i, uint32_t lk, uint32_t ld, bool flip, uint32_t &a,
+                                             uint32_t &b)
 {
     if (flip) {
-        const uint32_t half = k >> 1, blk = i / half, off = i % half;
-        a = blk * k + off;
-        b = blk * k + k - 1 - off;
+        const uint32_t blk = i >> (lk - 1), off = i & ((1u << (lk - 1)) - 1u);
+        a = (blk << lk) + off;
+        b = (blk << lk) + (1u << lk) - 1u - off;
     } else {
-        const uint32_t blk = i / d, off = i % d;
-        a = blk * 2 * d + off;
-        b = a + d;
+        const uint32_t blk = i >> ld, off = i & ((1u << ld) - 1u);
+        a = (blk << (ld + 1)) + off;
+        b = a + (1u << ld);
     }
 }
 
 __device__ __forceinline__ void smem_bitonic(uint64_t *s, uint32_t P)
 {
-    for (uint32_t k = 2; k <= P; k <<= 1) {
-        for (uint32_t d = k >> 1; d >= 1; d >>= 1) {
-            const bool flip = (d == (k >> 1));
+    const uint32_t lp = 31 - __clz(P);
+    for (uint32_t lk = 1; lk <= lp; lk++) {
+        for (int ld = (int)lk - 1; ld >= 0; ld--) {
+            const bool flip = (ld == (int)lk - 1);
             for (uint32_t i = threadIdx.x; i < P / 2; i += blockDim.x) {
                 uint32_t a, b;
-                bitonic_pair(i, k, d, flip, a, b);
-                uint64_t x = s[a], y = s[b];
+                bitonic_pair(i, lk, (uint32_t)ld, flip, a, b);
+                const uint64_t x = s[a], y = s[b];
                 if (y < x) {
                     s[a] = y;
                     s[b] = x;
@@ -228,12 +305,13 @@ k_sort_big(const uint32_t *__restrict__ ranges, uint64_t *__restrict__ keys, uin
             // in place in global memory; comparators reaching past the list compare
             // against the implicit padding and leave both sides unchanged
             uint64_t *k0 = keys + st;
-            for (uint32_t k = 2; k <= P; k <<= 1) {
-                for (uint32_t d = k >> 1; d >= 1; d >>= 1) {
-                    const bool flip = (d == (k >> 1));
+            const uint32_t lp = 31 - __clz(P);
+            for (uint32_t lk = 1; lk <= lp; lk++) {
+                for (int ld = (int)lk - 1; ld >= 0; ld--) {
+                    const bool flip = (ld == (int)lk - 1);
                     for (uint32_t i = threadIdx.x; i < P / 2; i += blockDim.x) {
                         uint32_t a, b;
-                        bitonic_pair(i, k, d, flip, a, b);
+                        bitonic_pair(i, lk, (uint32_t)ld, flip, a, b);
                         if (b >= len) continue;
                         uint64_t x = k0[a], y = k0[b];
                         if (y < x) {
@@ -290,11 +368,26 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
     cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (2 * (size_t)Ttot + 2), s);
     if (e != cudaSuccess) return e;
     const int64_t slots = (int64_t)V * n;
+    const size_t hist_bytes = sizeof(uint32_t) * (size_t)g.Tv;
+    const bool agg = hist_bytes <= kAggMaxSmem;
+    if (agg) {
+        e = cudaFuncSetAttribute(k_count_agg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hist_bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_scatter_agg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hist_bytes);
+        if (e != cudaSuccess) return e;
+    }
+    const dim3 agrid((unsigned)((n + kChunk - 1) / kChunk), (unsigned)V);
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((slots + threads - 1) / threads, (int64_t)num_sms * 16);
-    k_count<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count);
+    if (agg)
+        k_count_agg<<<agrid, kAggThreads, hist_bytes, s>>>(r4, n, g, w.count);
+    else
+        k_count<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count);
     k_scan<<<1, 1024, 0, s>>>(w.count, Ttot, capacity, ranges, n_inst, status);
-    k_scatter<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count, w.cursor, w.keys, capacity);
+    if (agg)
+        k_scatter_agg<<<agrid, kAggThreads, hist_bytes, s>>>(r4, n, g, w.count, w.cursor, w.keys, capacity);
+    else
+        k_scatter<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count, w.cursor, w.keys, capacity);
     k_sort_small<<<(unsigned)Ttot, kSmallThreads, 0, s>>>(ranges, w.keys, vals, w.big, w.nbig);
     const size_t big_smem = sizeof(uint64_t) * kBigCap;
     e = cudaFuncSetAttribute(k_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem);

@@ -48,6 +48,75 @@ __device__ __forceinline__ void item_tile(const uint32_t *order, const Grid &g, 
     tx = t - ty * g.Tx;
 }
 
+// Conservative tile test of a staged splat: can it reach alpha >= 1/255 at any pixel
+// centre of the box [bx0, bx1] x [by0, by1]?  alpha = o exp(power) <= o (power <= 0), so
+// a splat with o < 1/255 is skipped by every pixel; otherwise alpha >= 1/255 needs
+// q = d^T Q d <= 2 ln(255 o), an ellipse whose axis-aligned half-extents are
+// sqrt(2 ln(255 o) (Q^-1)_xx) and sqrt(2 ln(255 o) (Q^-1)_yy), (Q^-1)_xx = C/det(Q).
+// The margins (relative 1e-3 on the bound, 1e-3 absolute, 1e-2 px) exceed the float32
+// error of the per-pixel test, so a culled splat is one every pixel of the tile skips:
+// culling changes no decision of the forward or backward.
+__device__ __forceinline__ bool splat_touches_box(const float4 &r0, const float4 &r1, float bx0, float bx1,
+                                                  float by0, float by1)
+{
+    const float o = r1.y;
+    if (o * 255.0f < 0.9999f) return false;
+    const float A = r0.z, B = r0.w, C = r1.x;
+    const float det = A * C - B * B;
+    if (!(det > 0.f)) return true;
+    const float t2 = 2.0f * logf(255.0f * o) * 1.001f + 1e-3f;
+    const float ex = sqrtf(t2 * C / det) + 1e-2f, ey = sqrtf(t2 * A / det) + 1e-2f;
+    const float dx = fabsf(r0.x - fminf(fmaxf(r0.x, bx0), bx1));
+    const float dy = fabsf(r0.y - fminf(fmaxf(r0.y, by0), by1));
+    return dx <= ex && dy <= ey;
+}
+
+// Exclusive prefix count of `keep` over the threads of the block (thread order) and the
+// block total; NW = warps per block.  Contains two barriers.
+template <int NW>
+__device__ __forceinline__ int block_compact(bool keep, int *wcnt, int &total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned b = __ballot_sync(kFull, keep);
+    if (lane == 0) wcnt[w] = __popc(b);
+    __syncthreads();
+    int off = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < NW; i++) {
+        const int c = wcnt[i];
+        off += (i < w) ? c : 0;
+        tot += c;
+    }
+    total = tot;
+    const int pre = off + __popc(b & ((1u << lane) - 1u));
+    __syncthreads();
+    return pre;
+}
+
+// Pixels per thread in the raster kernels: a thread owns PPT vertically adjacent pixels,
+// so the staged splat is read from shared memory once for PPT pixels and the backward's
+// per-(warp, splat) reduction covers 32*PPT pixels.
+constexpr int kPPT = 2;
+
+// Staged splat, derived exactly from its record (negation and scaling by 1/2 are exact):
+//   s0 = (u, v, -A/2, -B), s1 = (-C/2, opacity, depth, tau), s2 = (r, g, b, -)
+// where tau = -ln(255 opacity): alpha = opacity exp(power) < 1/255 exactly when
+// power < tau, so both raster kernels test the exponent against tau and evaluate the
+// exponential only for pairs that can blend.
+__device__ __forceinline__ void stage_splat(const float4 &r0, const float4 &r1, float4 &t0, float4 &t1)
+{
+    t0 = make_float4(r0.x, r0.y, -0.5f * r0.z, -r0.w);
+    t1 = make_float4(-0.5f * r1.x, r1.y, r1.z, -logf(255.0f * r1.y));
+}
+
+// Exponent of the projected Gaussian at a pixel from a staged splat, with explicit
+// roundings so both raster kernels compute the same bits:
+//   power = dx (-A/2 dx - B dy) + (-C/2 dy) dy,  dx = u - x, dy = v - y.
+__device__ __forceinline__ float staged_power(const float4 &t0, float hC, float dx, float dy)
+{
+    return fmaf(dx, fmaf(t0.z, dx, __fmul_rn(t0.w, dy)), __fmul_rn(__fmul_rn(hC, dy), dy));
+}
+
 cudaError_t raster_fwd(const RasterFwdArgs &a, int B, int BD, cudaStream_t s);
 cudaError_t raster_bwd(const RasterBwdArgs &a, int B, int BD, cudaStream_t s);
 

@@ -1,17 +1,19 @@
 // Backward of the blend (Eqs. 2-4, Sec. III-C.1, CaRtGS), pixel-parallel.
 //
-// One block per (view, tile), one thread per pixel, walking the tile's list back
-// to front from the block's largest `last`.  Each pixel recomputes alpha exactly as
+// One block per (view, tile), two vertically adjacent pixels per thread, walking the
+// tile's list back to front from the block's largest `last`.  Staging applies the
+// forward's tile test and exponent threshold, so the same splats are considered.  Each pixel recomputes alpha exactly as
 // the forward did (same rounding, same decisions) and its transmittance from the
 // stored final T, T_j = T_{j+1} / (1 - alpha_j), so no per-pixel splat list is kept.
 // The accumulated colour behind splat j follows acc_j = a_{j+1} c_{j+1} +
 // (1 - a_{j+1}) acc_{j+1}, and
 //   dL/dalpha_j = T_j sum_c gI_c (c_j - acc_j) + T_j gD (z_j - accD_j)
 //                 - T_final (bg . gI) / (1 - alpha_j).
-// The per-(splat, pixel) gradients of the 32 pixels of a warp are summed with a
-// butterfly reduce-scatter (15 shuffles for 10 fields instead of 50 for a plain
-// tree per field), after which ten lanes each issue one atomic add into the
-// slot's gradient record.  Warps where no pixel blended the splat skip it (vote).
+// The per-(splat, pixel) gradients of a thread's two pixels are added in registers,
+// then the 64 pixels of a warp are summed with a butterfly reduce-scatter (15 shuffles
+// for 10 fields instead of 50 for a plain tree per field), after which ten lanes each
+// issue one atomic add into the slot's gradient record.  Warps where no pixel blended
+// the splat skip it (vote).
 #include "raster.cuh"
 
 namespace cgs {
@@ -55,125 +57,157 @@ __device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane)
 }
 
 template <int B, int BD>
-__global__ void __launch_bounds__(B *B) k_render_bwd(RasterBwdArgs a)
+__global__ void __launch_bounds__(B *B / kPPT) k_render_bwd(RasterBwdArgs a)
 {
-    constexpr int NT = B * B;
+    constexpr int NT = B * B / kPPT;
     constexpr int NW = NT / 32;
     __shared__ float4 s0[BD], s1[BD], s2[BD];
-    __shared__ uint32_t sslot[BD];
+    __shared__ uint32_t sslot[BD], spos[BD];
     __shared__ uint32_t smax[NW];
+    __shared__ int wcnt[NW];
     int64_t tile;
     int view, tx, ty;
     item_tile(a.order, a.g, tile, view, tx, ty);
     const int lane = threadIdx.x & 31;
-    const int px = tx * B + (int)(threadIdx.x % B), py = ty * B + (int)(threadIdx.x / B);
-    const bool inside = px < a.g.W && py < a.g.H;
-    const float fx = (float)px, fy = (float)py;
+    const int px = tx * B + (int)(threadIdx.x % B);
+    const int py0 = ty * B + (int)(threadIdx.x / B) * kPPT;
+    const float fx = (float)px;
+    const uint32_t start = a.ranges[2 * tile];
+    const uint32_t len = a.ranges[2 * tile + 1] - start;
+    const size_t HW = (size_t)a.g.W * a.g.H;
 
-    uint32_t lst = 0;
-    float T = 1.f, gI0 = 0.f, gI1 = 0.f, gI2 = 0.f, gD = 0.f, bgdot = 0.f;
-    if (inside) {
-        const size_t HW = (size_t)a.g.W * a.g.H;
-        const size_t p = (size_t)py * a.g.W + px;
-        const size_t pix = (size_t)view * HW + p;
-        lst = a.last[pix];
-        T = a.tfin[pix];
+    // per-pixel state
+    float fy[kPPT], T[kPPT], gI0[kPPT], gI1[kPPT], gI2[kPPT], gD[kPPT], bgdot[kPPT];
+    float acc0[kPPT], acc1[kPPT], acc2[kPPT], accD[kPPT], la[kPPT], lc0[kPPT], lc1[kPPT], lc2[kPPT], lz[kPPT];
+    uint32_t lst[kPPT];
+    uint32_t m = 0;
+#pragma unroll
+    for (int p = 0; p < kPPT; p++) {
+        const int py = py0 + p;
+        fy[p] = (float)py;
+        lst[p] = 0;
+        T[p] = 1.f;
+        gI0[p] = gI1[p] = gI2[p] = gD[p] = bgdot[p] = 0.f;
+        acc0[p] = acc1[p] = acc2[p] = accD[p] = 0.f;
+        la[p] = lc0[p] = lc1[p] = lc2[p] = lz[p] = 0.f;
+        if (!(px < a.g.W && py < a.g.H)) continue;
+        const size_t q = (size_t)py * a.g.W + px;
+        const size_t pix = (size_t)view * HW + q;
+        // never walk past the tile's list, whatever `last` holds
+        lst[p] = min(a.last[pix], len);
+        T[p] = a.tfin[pix];
         if (a.dl_dimg) {
-            const float *gi = a.dl_dimg + (size_t)view * 3 * HW + p;
-            gI0 = gi[0];
-            gI1 = gi[HW];
-            gI2 = gi[2 * HW];
-            gD = a.dl_ddepth ? a.dl_ddepth[pix] : 0.f;
+            const float *gi = a.dl_dimg + (size_t)view * 3 * HW + q;
+            gI0[p] = gi[0];
+            gI1[p] = gi[HW];
+            gI2[p] = gi[2 * HW];
+            gD[p] = a.dl_ddepth ? a.dl_ddepth[pix] : 0.f;
         } else {
             const float w = a.weight ? a.weight[view] : 1.f;
-            const float s = w / (3.f * (float)HW);
-            const float *im = a.img + (size_t)view * 3 * HW + p;
-            const float *tr = a.tgt_rgb + (size_t)view * 3 * HW + p;
-            gI0 = s * sgnf(im[0] - tr[0]);
-            gI1 = s * sgnf(im[HW] - tr[HW]);
-            gI2 = s * sgnf(im[2 * HW] - tr[2 * HW]);
+            const float sc = w / (3.f * (float)HW);
+            const float *im = a.img + (size_t)view * 3 * HW + q;
+            const float *tr = a.tgt_rgb + (size_t)view * 3 * HW + q;
+            gI0[p] = sc * sgnf(im[0] - tr[0]);
+            gI1[p] = sc * sgnf(im[HW] - tr[HW]);
+            gI2[p] = sc * sgnf(im[2 * HW] - tr[2 * HW]);
             if (a.tgt_depth) {
                 const float td = a.tgt_depth[pix];
                 const int cnt = a.depth_count[view];
-                if (td > 0.f && cnt > 0) gD = w * a.lambda_d * sgnf(a.depth[pix] - td) / (float)cnt;
+                if (td > 0.f && cnt > 0) gD[p] = w * a.lambda_d * sgnf(a.depth[pix] - td) / (float)cnt;
             }
         }
-        bgdot = T * (a.bg0 * gI0 + a.bg1 * gI1 + a.bg2 * gI2);
+        bgdot[p] = T[p] * (a.bg0 * gI0[p] + a.bg1 * gI1[p] + a.bg2 * gI2[p]);
+        m = max(m, lst[p]);
     }
-    // never walk past the tile's list, whatever `last` holds
-    const uint32_t start = a.ranges[2 * tile];
-    const uint32_t len = a.ranges[2 * tile + 1] - start;
-    lst = min(lst, len);
     // block-wide largest `last`: the walk starts there
-    uint32_t m = lst;
     for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(kFull, m, off));
     if (lane == 0) smax[threadIdx.x / 32] = m;
     __syncthreads();
     uint32_t maxlast = 0;
     for (int i = 0; i < NW; i++) maxlast = max(maxlast, smax[i]);
 
-    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, accD = 0.f;
-    float la = 0.f, lc0 = 0.f, lc1 = 0.f, lc2 = 0.f, lz = 0.f;
+    const float bx0 = (float)(tx * B), bx1 = (float)(min(tx * B + B, a.g.W) - 1);
+    const float by0 = (float)(ty * B), by1 = (float)(min(ty * B + B, a.g.H) - 1);
     for (int bend = (int)maxlast; bend > 0; bend -= BD) {
         const int bstart = max(0, bend - BD);
-        const int cnt = bend - bstart;
+        const int nraw = bend - bstart;
         __syncthreads();
-        for (int i = threadIdx.x; i < cnt; i += NT) {
-            const uint32_t slot = __ldg(a.vals + start + bstart + i);
-            const float4 *r = a.rec + kRec4 * (size_t)slot;
-            sslot[i] = slot;
-            s0[i] = __ldg(r);
-            s1[i] = __ldg(r + 1);
-            s2[i] = __ldg(r + 2);
+        // stage positions [bstart, bend), keeping in list order only splats that can
+        // touch the tile (the forward applied the same test)
+        int cnt = 0;
+        for (int c0 = 0; c0 < BD; c0 += NT) {
+            const int i = c0 + (int)threadIdx.x;
+            bool keep = false;
+            float4 r0, r1;
+            const float4 *r = nullptr;
+            uint32_t slot = 0;
+            if (i < nraw) {
+                slot = __ldg(a.vals + start + bstart + i);
+                r = a.rec + kRec4 * (size_t)slot;
+                r0 = __ldg(r);
+                r1 = __ldg(r + 1);
+                keep = splat_touches_box(r0, r1, bx0, bx1, by0, by1);
+            }
+            int tot;
+            const int pre = block_compact<NW>(keep, wcnt, tot);
+            if (keep) {
+                const int d = cnt + pre;
+                stage_splat(r0, r1, s0[d], s1[d]);
+                s2[d] = __ldg(r + 2);
+                sslot[d] = slot;
+                spos[d] = (uint32_t)(bstart + i);
+            }
+            cnt += tot;
         }
         __syncthreads();
         for (int j = cnt - 1; j >= 0; j--) {
-            const uint32_t pos = (uint32_t)(bstart + j);
+            const uint32_t pos = spos[j];
+            const float4 q0 = s0[j];
+            const float4 q1 = s1[j];
+            const float dx = __fsub_rn(q0.x, fx);
             float v[16];
 #pragma unroll
             for (int k = 0; k < 16; k++) v[k] = 0.f;
             bool contrib = false;
-            if (pos < lst) {
-                const float4 q0 = s0[j];
-                const float4 q1 = s1[j];
-                float dx, dy;
-                const float power = splat_power(q0.x, q0.y, q0.z, q0.w, q1.x, fx, fy, dx, dy);
-                if (!(power > 0.f)) {
-                    const float G = __expf(power);
-                    const float araw = __fmul_rn(q1.y, G);
-                    const float alpha = fminf(kAlphaMax, araw);
-                    if (!(alpha < kAlphaMin)) {
-                        contrib = true;
-                        const float4 q2 = s2[j];
-                        const float om = __fsub_rn(1.f, alpha);
-                        T = __fmul_rn(T, __frcp_rn(om));          // transmittance before splat j
-                        acc0 = fmaf(la, lc0 - acc0, acc0);         // colour behind splat j
-                        acc1 = fmaf(la, lc1 - acc1, acc1);
-                        acc2 = fmaf(la, lc2 - acc2, acc2);
-                        accD = fmaf(la, lz - accD, accD);
-                        la = alpha;
-                        lc0 = q2.x;
-                        lc1 = q2.y;
-                        lc2 = q2.z;
-                        lz = q1.z;
-                        const float wT = alpha * T;
-                        v[8] = wT * gI0;
-                        v[9] = wT * gI1;
-                        v[10] = wT * gI2;
-                        v[6] = wT * gD;
-                        float dLda = (q2.x - acc0) * gI0 + (q2.y - acc1) * gI1 + (q2.z - acc2) * gI2 +
-                                     (q1.z - accD) * gD;
-                        dLda = dLda * T - bgdot / om;
-                        if (!(araw > kAlphaMax)) {
-                            const float dp = dLda * alpha;          // dalpha/dpower = alpha
-                            v[5] = dLda * G;                        // dalpha/dopacity = G
-                            v[0] = -dp * (q0.z * dx + q0.w * dy);
-                            v[1] = -dp * (q1.x * dy + q0.w * dx);
-                            v[2] = -0.5f * dp * dx * dx;
-                            v[3] = -dp * dx * dy;
-                            v[4] = -0.5f * dp * dy * dy;
-                        }
-                    }
+#pragma unroll
+            for (int p = 0; p < kPPT; p++) {
+                if (!(pos < lst[p])) continue;
+                const float dy = __fsub_rn(q0.y, fy[p]);
+                const float power = staged_power(q0, q1.x, dx, dy);
+                if (power > 0.f || power < q1.w) continue;
+                const float G = __expf(power);
+                const float araw = __fmul_rn(q1.y, G);
+                const float alpha = fminf(kAlphaMax, araw);
+                contrib = true;
+                const float4 q2 = s2[j];
+                const float inv_om = __frcp_rn(__fsub_rn(1.f, alpha));
+                T[p] = __fmul_rn(T[p], inv_om);                  // transmittance before splat j
+                acc0[p] = fmaf(la[p], lc0[p] - acc0[p], acc0[p]);  // colour behind splat j
+                acc1[p] = fmaf(la[p], lc1[p] - acc1[p], acc1[p]);
+                acc2[p] = fmaf(la[p], lc2[p] - acc2[p], acc2[p]);
+                accD[p] = fmaf(la[p], lz[p] - accD[p], accD[p]);
+                la[p] = alpha;
+                lc0[p] = q2.x;
+                lc1[p] = q2.y;
+                lc2[p] = q2.z;
+                lz[p] = q1.z;
+                const float wT = alpha * T[p];
+                v[8] += wT * gI0[p];
+                v[9] += wT * gI1[p];
+                v[10] += wT * gI2[p];
+                v[6] += wT * gD[p];
+                float dLda = (q2.x - acc0[p]) * gI0[p] + (q2.y - acc1[p]) * gI1[p] + (q2.z - acc2[p]) * gI2[p] +
+                             (q1.z - accD[p]) * gD[p];
+                dLda = dLda * T[p] - bgdot[p] * inv_om;
+                if (!(araw > kAlphaMax)) {
+                    const float dp = dLda * alpha;          // dalpha/dpower = alpha
+                    v[5] += dLda * G;                       // dalpha/dopacity = G
+                    // staged q0.z = -A/2, q0.w = -B, q1.x = -C/2
+                    v[0] += dp * (2.f * q0.z * dx + q0.w * dy);   // -(A dx + B dy)
+                    v[1] += dp * (2.f * q1.x * dy + q0.w * dx);   // -(C dy + B dx)
+                    v[2] += -0.5f * dp * dx * dx;
+                    v[3] += -dp * dx * dy;
+                    v[4] += -0.5f * dp * dy * dy;
                 }
             }
             if (__any_sync(kFull, contrib)) {
@@ -189,7 +223,7 @@ template <int B, int BD>
 static cudaError_t launch_bwd(const RasterBwdArgs &a, cudaStream_t s)
 {
     const int64_t items = a.g.Tv * a.V;
-    k_render_bwd<B, BD><<<(unsigned)items, B * B, 0, s>>>(a);
+    k_render_bwd<B, BD><<<(unsigned)items, B * B / kPPT, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -1,96 +1,140 @@
 // Forward blend of Eq. 1 (Sec. III-B, CaRtGS) with the L1 loss fused in.
 //
-// One block per (view, tile), one thread per pixel.  The tile's depth-sorted list
-// is consumed in batches of BD splats: the block gathers the records of a batch
-// into shared memory (one coalesced 48-byte record per thread), then every pixel
-// walks the batch front to back.  A block-wide vote (__syncthreads_count) ends the
-// walk as soon as every pixel of the tile is saturated (T below 1e-4) or done.
+// One block per (view, tile), two vertically adjacent pixels per thread.  The tile's
+// depth-sorted list is consumed in batches of BD splats: the block gathers the
+// records of a batch (48 bytes each, one per thread), drops splats whose
+// alpha >= 1/255 ellipse misses the tile (exact-safe, see splat_touches_box), and
+// compacts the survivors in list order into shared memory; every pixel then walks
+// the batch front to back, rejecting a pair on its exponent (power < tau) before any
+// exponential.  A block-wide vote (__syncthreads_count) ends the walk as soon as every
+// pixel of the tile is saturated (T below 1e-4).
 #include "raster.cuh"
 
 namespace cgs {
 
 template <int B, int BD>
-__global__ void __launch_bounds__(B *B) k_render_fwd(RasterFwdArgs a)
+__global__ void __launch_bounds__(B *B / kPPT) k_render_fwd(RasterFwdArgs a)
 {
-    constexpr int NT = B * B;
+    constexpr int NT = B * B / kPPT;
     constexpr int NW = NT / 32;
     __shared__ float4 s0[BD], s1[BD], s2[BD];
-    __shared__ float red[5][NW > 0 ? NW : 1];
+    __shared__ uint32_t spos[BD];
+    __shared__ int wcnt[NW];
+    __shared__ float red[5][NW];
     int64_t tile;
     int view, tx, ty;
     item_tile(a.order, a.g, tile, view, tx, ty);
-    const int px = tx * B + (int)(threadIdx.x % B), py = ty * B + (int)(threadIdx.x / B);
-    const bool inside = px < a.g.W && py < a.g.H;
+    const int px = tx * B + (int)(threadIdx.x % B);
+    const int py0 = ty * B + (int)(threadIdx.x / B) * kPPT;
     const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
-    const float fx = (float)px, fy = (float)py;
+    const float fx = (float)px;
+    // pixel-centre box of the tile (clipped to the image)
+    const float bx0 = (float)(tx * B), bx1 = (float)(min(tx * B + B, a.g.W) - 1);
+    const float by0 = (float)(ty * B), by1 = (float)(min(ty * B + B, a.g.H) - 1);
 
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-    uint32_t lst = 0, n_eval = 0, n_blend = 0;
-    bool done = !inside;
+    float fy[kPPT], T[kPPT], C0[kPPT], C1[kPPT], C2[kPPT], D[kPPT];
+    uint32_t lst[kPPT];
+    bool done[kPPT];
+    bool tdone = true;
+#pragma unroll
+    for (int p = 0; p < kPPT; p++) {
+        fy[p] = (float)(py0 + p);
+        T[p] = 1.f;
+        C0[p] = C1[p] = C2[p] = D[p] = 0.f;
+        lst[p] = 0;
+        done[p] = !(px < a.g.W && py0 + p < a.g.H);
+        tdone = tdone && done[p];
+    }
+    uint32_t n_eval = 0, n_blend = 0;
     for (uint32_t base = start; base < end; base += BD) {
-        if (__syncthreads_count(!done) == 0) break;
-        for (int i = threadIdx.x; i < BD; i += NT) {
-            const uint32_t idx = base + i;
-            if (idx < end) {
-                const float4 *r = a.rec + kRec4 * (size_t)__ldg(a.vals + idx);
-                s0[i] = __ldg(r);
-                s1[i] = __ldg(r + 1);
-                s2[i] = __ldg(r + 2);
+        if (__syncthreads_count(!tdone) == 0) break;
+        // stage the batch, keeping (in list order) only splats that can touch the tile
+        int cnt = 0;
+        for (int c0 = 0; c0 < BD; c0 += NT) {
+            const int i = c0 + (int)threadIdx.x;
+            const uint32_t idx = base + (uint32_t)i;
+            bool keep = false;
+            float4 r0, r1;
+            const float4 *r = nullptr;
+            if (i < BD && idx < end) {
+                r = a.rec + kRec4 * (size_t)__ldg(a.vals + idx);
+                r0 = __ldg(r);
+                r1 = __ldg(r + 1);
+                keep = splat_touches_box(r0, r1, bx0, bx1, by0, by1);
             }
+            int tot;
+            const int pre = block_compact<NW>(keep, wcnt, tot);
+            if (keep) {
+                const int d = cnt + pre;
+                stage_splat(r0, r1, s0[d], s1[d]);
+                s2[d] = __ldg(r + 2);
+                spos[d] = idx - start;
+            }
+            cnt += tot;
         }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)BD, end - base);
-        if (!done) {
-            int j = 0;
-            for (; j < cnt; j++) {
+        if (!tdone) {
+            for (int j = 0; j < cnt; j++) {
                 const float4 q0 = s0[j];
                 const float4 q1 = s1[j];
-                float dx, dy;
-                const float power = splat_power(q0.x, q0.y, q0.z, q0.w, q1.x, fx, fy, dx, dy);
-                if (power > 0.f) continue;
-                const float alpha = fminf(kAlphaMax, __fmul_rn(q1.y, __expf(power)));
-                if (alpha < kAlphaMin) continue;
-                const float testT = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                if (testT < kTMin) {
-                    done = true;
-                    j++;
-                    break;
+                const float dx = __fsub_rn(q0.x, fx);
+                bool all = true;
+#pragma unroll
+                for (int p = 0; p < kPPT; p++) {
+                    if (done[p]) continue;
+                    n_eval++;
+                    const float dy = __fsub_rn(q0.y, fy[p]);
+                    const float power = staged_power(q0, q1.x, dx, dy);
+                    all = false;
+                    if (power > 0.f || power < q1.w) continue;
+                    const float alpha = fminf(kAlphaMax, __fmul_rn(q1.y, __expf(power)));
+                    const float testT = __fmul_rn(T[p], __fsub_rn(1.f, alpha));
+                    if (testT < kTMin) {
+                        done[p] = true;
+                        continue;
+                    }
+                    const float wgt = __fmul_rn(alpha, T[p]);
+                    const float4 q2 = s2[j];
+                    C0[p] = fmaf(q2.x, wgt, C0[p]);
+                    C1[p] = fmaf(q2.y, wgt, C1[p]);
+                    C2[p] = fmaf(q2.z, wgt, C2[p]);
+                    D[p] = fmaf(q1.z, wgt, D[p]);
+                    T[p] = testT;
+                    lst[p] = spos[j] + 1u;
+                    n_blend++;
                 }
-                const float wgt = __fmul_rn(alpha, T);
-                const float4 q2 = s2[j];
-                C0 = fmaf(q2.x, wgt, C0);
-                C1 = fmaf(q2.y, wgt, C1);
-                C2 = fmaf(q2.z, wgt, C2);
-                D = fmaf(q1.z, wgt, D);
-                T = testT;
-                lst = base - start + (uint32_t)j + 1u;
-                n_blend++;
+                if (all) break;
             }
-            n_eval += (uint32_t)j;
+            tdone = true;
+#pragma unroll
+            for (int p = 0; p < kPPT; p++) tdone = tdone && done[p];
         }
     }
 
     float l_rgb = 0.f, l_d = 0.f, c_d = 0.f;
-    if (inside) {
-        const size_t HW = (size_t)a.g.W * a.g.H;
-        const size_t p = (size_t)py * a.g.W + px;
-        const size_t pix = (size_t)view * HW + p;
-        const float I0 = fmaf(T, a.bg0, C0), I1 = fmaf(T, a.bg1, C1), I2 = fmaf(T, a.bg2, C2);
-        float *im = a.img + (size_t)view * 3 * HW + p;
+    const size_t HW = (size_t)a.g.W * a.g.H;
+#pragma unroll
+    for (int p = 0; p < kPPT; p++) {
+        const int py = py0 + p;
+        if (!(px < a.g.W && py < a.g.H)) continue;
+        const size_t q = (size_t)py * a.g.W + px;
+        const size_t pix = (size_t)view * HW + q;
+        const float I0 = fmaf(T[p], a.bg0, C0[p]), I1 = fmaf(T[p], a.bg1, C1[p]), I2 = fmaf(T[p], a.bg2, C2[p]);
+        float *im = a.img + (size_t)view * 3 * HW + q;
         im[0] = I0;
         im[HW] = I1;
         im[2 * HW] = I2;
-        a.depth[pix] = D;
-        a.tfin[pix] = T;
-        a.last[pix] = lst;
+        a.depth[pix] = D[p];
+        a.tfin[pix] = T[p];
+        a.last[pix] = lst[p];
         if (a.tgt_rgb) {
-            const float *tr = a.tgt_rgb + (size_t)view * 3 * HW + p;
-            l_rgb = fabsf(I0 - tr[0]) + fabsf(I1 - tr[HW]) + fabsf(I2 - tr[2 * HW]);
+            const float *tr = a.tgt_rgb + (size_t)view * 3 * HW + q;
+            l_rgb += fabsf(I0 - tr[0]) + fabsf(I1 - tr[HW]) + fabsf(I2 - tr[2 * HW]);
             if (a.tgt_depth) {
                 const float td = a.tgt_depth[pix];
                 if (td > 0.f) {
-                    l_d = fabsf(D - td);
-                    c_d = 1.f;
+                    l_d += fabsf(D[p] - td);
+                    c_d += 1.f;
                 }
             }
         }
@@ -162,7 +206,7 @@ template <int B, int BD>
 static cudaError_t launch_fwd(const RasterFwdArgs &a, cudaStream_t s)
 {
     const int64_t items = a.g.Tv * a.V;
-    k_render_fwd<B, BD><<<(unsigned)items, B * B, 0, s>>>(a);
+    k_render_fwd<B, BD><<<(unsigned)items, B * B / kPPT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
