@@ -180,8 +180,8 @@ __global__ void __launch_bounds__(B *B / kPPT) k_render_bwd(RasterBwdArgs a)
                 const float alpha = fminf(kAlphaMax, araw);
                 contrib = true;
                 const float4 q2 = s2[j];
-                const float inv_om = __frcp_rn(__fsub_rn(1.f, alpha));
-                T[p] = __fmul_rn(T[p], inv_om);                  // transmittance before splat j
+                const float inv_om = __fdividef(1.f, __fsub_rn(1.f, alpha));
+                T[p] = T[p] * inv_om;                             // transmittance before splat j
                 acc0[p] = fmaf(la[p], lc0[p] - acc0[p], acc0[p]);  // colour behind splat j
                 acc1[p] = fmaf(la[p], lc1[p] - acc1[p], acc1[p]);
                 acc2[p] = fmaf(la[p], lc2[p] - acc2[p], acc2[p]);
@@ -200,19 +200,34 @@ __global__ void __launch_bounds__(B *B / kPPT) k_render_bwd(RasterBwdArgs a)
                              (q1.z - accD[p]) * gD[p];
                 dLda = dLda * T[p] - bgdot[p] * inv_om;
                 if (!(araw > kAlphaMax)) {
-                    const float dp = dLda * alpha;          // dalpha/dpower = alpha
-                    v[5] += dLda * G;                       // dalpha/dopacity = G
-                    // staged q0.z = -A/2, q0.w = -B, q1.x = -C/2
-                    v[0] += dp * (2.f * q0.z * dx + q0.w * dy);   // -(A dx + B dy)
-                    v[1] += dp * (2.f * q1.x * dy + q0.w * dx);   // -(C dy + B dx)
-                    v[2] += -0.5f * dp * dx * dx;
-                    v[3] += -dp * dx * dy;
-                    v[4] += -0.5f * dp * dy * dy;
+                    // dalpha/dpower = alpha, dalpha/dopacity = G.  Raw moments of
+                    // dp = dL/dpower are summed here; the conic / centre gradients are
+                    // formed from them once per warp after the reduction.
+                    const float dp = dLda * alpha;
+                    v[5] += dLda * G;
+                    const float dpx = dp * dx, dpy = dp * dy;
+                    v[0] += dpx;             // sum dp dx
+                    v[1] += dpy;             // sum dp dy
+                    v[2] += dpx * dx;        // sum dp dx^2
+                    v[3] += dpx * dy;        // sum dp dx dy
+                    v[4] += dpy * dy;        // sum dp dy^2
                 }
             }
             if (__any_sync(kFull, contrib)) {
-                const float sum = warp_reduce_scatter16(v, lane);
+                float sum = warp_reduce_scatter16(v, lane);
                 const int f = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+                // fields 0 and 1 sit in lanes that differ in bit 1: exchange the two first moments
+                const float other = __shfl_xor_sync(kFull, sum, 2);
+                // power = -(A dx^2 + C dy^2)/2 - B dx dy with dx = u - x:
+                //   dL/du = -(A S_dx + B S_dy), dL/dv = -(C S_dy + B S_dx),
+                //   dL/dA = -S_xx / 2, dL/dB = -S_xy, dL/dC = -S_yy / 2
+                // (staged q0.z = -A/2, q0.w = -B, q1.x = -C/2)
+                const float4 q0 = s0[j];
+                const float hC = s1[j].x;
+                if (f == 0) sum = 2.f * q0.z * sum + q0.w * other;
+                else if (f == 1) sum = 2.f * hC * sum + q0.w * other;
+                else if (f == 2 || f == 4) sum = -0.5f * sum;
+                else if (f == 3) sum = -sum;
                 if (!(lane & 1) && f != 7 && f < 11) atomicAdd(a.sgrad + (size_t)sslot[j] * 12 + f, sum);
             }
         }
