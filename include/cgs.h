@@ -171,6 +171,29 @@ int cgs_render_fwd(const float *rec, const uint32_t *vals, const uint32_t *range
                    int32_t *status_dev, void *stream);
 
 /*
+ * cgs_render_fwd_noalloc -- cgs_render_fwd for callers that cannot allocate device
+ * memory or pass a workspace: for instance a real-time mapping loop that must not
+ * allocate once running (an allocation can block on the driver and miss the frame
+ * budget), or glue code that only receives another framework's input and output
+ * buffers.  The paper has no counterpart; it is an interface convenience.
+ * Same arguments and results as cgs_render_fwd without the workspace.  The per-tile
+ * partial sums live in one library-resident device array for at most 65536 tiles
+ * (V * tiles_per_view; larger windows return CGS_ERR_WORKSPACE and launch nothing),
+ * held on every GPU that loads the library until the process exits.
+ *  - The first call on a device looks up that array's device address (with the device
+ *    current) and caches it; make that first call before any stream capture.
+ *  - The call allocates nothing (no cudaMalloc, cudaFree or allocating library call).
+ *  - All calls share the one array, which keeps the last call's contents; each call
+ *    writes every entry it reads, so nothing needs clearing, but calls that overlap
+ *    on the GPU (different streams, or different host threads) race on it.
+ */
+int cgs_render_fwd_noalloc(const float *rec, const uint32_t *vals, const uint32_t *ranges,
+                           const uint32_t *tile_order, int32_t V, const cgs_config *cfg,
+                           const float *view_weight, const float *tgt_rgb, const float *tgt_depth,
+                           float *img, float *depth, float *t_final, uint32_t *last, float *loss_view,
+                           int32_t *depth_count, int32_t *status_dev, void *stream);
+
+/*
  * cgs_raster_bwd -- backward of the blend (Eqs. 2-4, Sec. III-C.1), pixel-parallel,
  * back to front from `last`, with the transmittance recomputed from the stored
  * final T (T_j = T_{j+1} / (1 - alpha_j)) instead of stored per-pixel lists.  Per

@@ -58,6 +58,8 @@ _SIGS = {
     "cgs_render_fwd_workspace": (c_size_t, [c_int32, _P]),
     "cgs_render_fwd": (c_int32, [_P, _P, _P, _P, c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                  c_size_t, _P, _P]),
+    "cgs_render_fwd_noalloc": (c_int32, [_P, _P, _P, _P, c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                         _P, _P]),
     "cgs_raster_bwd": (c_int32, [_P, _P, _P, _P, c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                  _P, _P, _P]),
     "cgs_preprocess_bwd": (c_int32, [_P, c_int64, _P, c_int32, _P, _P, _P, _P, c_int32, _P, _P, _P,
@@ -167,6 +169,16 @@ def cgs_render_fwd(rec, vals, ranges, tile_order, V, cfg, view_weight, tgt_rgb, 
         _dev(rec), _dev(vals), _dev(ranges), _dev(tile_order), V, byref(cfg), _dev(view_weight),
         _dev(tgt_rgb), _dev(tgt_depth), _dev(img), _dev(depth), _dev(t_final), _dev(last),
         _dev(loss_view), _dev(depth_count), _dev(workspace), nbytes, _dev(status), _stream(stream)))
+
+
+def cgs_render_fwd_noalloc(rec, vals, ranges, tile_order, V, cfg, view_weight, tgt_rgb, tgt_depth, img, depth,
+                           t_final, last, loss_view, depth_count, status=None, stream=None):
+    """cgs_render_fwd with the library's built-in scratch (no workspace argument); for
+    callers that cannot allocate.  Windows above 65536 tiles are refused."""
+    _check("cgs_render_fwd_noalloc", lib().cgs_render_fwd_noalloc(
+        _dev(rec), _dev(vals), _dev(ranges), _dev(tile_order), V, byref(cfg), _dev(view_weight),
+        _dev(tgt_rgb), _dev(tgt_depth), _dev(img), _dev(depth), _dev(t_final), _dev(last),
+        _dev(loss_view), _dev(depth_count), _dev(status), _stream(stream)))
 
 
 def cgs_raster_bwd(rec, vals, ranges, tile_order, V, cfg, view_weight, img, depth, t_final, last, tgt_rgb,

@@ -239,3 +239,96 @@ cudaError_t loss_reduce(const float *partials, const Grid &g, int V, const float
 }
 
 }  // namespace cgs
+
+// ---------------------------------------------------------------------------------
+// cgs_render_fwd_noalloc: the forward render with its scratch inside the library.
+//
+// Some callers cannot hand the library a workspace: a real-time mapping thread that
+// must not allocate once it is running (a device allocation can block on the driver
+// and miss the frame budget), or code that only ever sees the input and output
+// buffers of another framework.  For them the per-tile partial sums live in this
+// file-scope device array, sized for kNoAllocMaxTiles tiles (V * tiles per view);
+// every GPU that loads the library holds it until the process exits.
+// ---------------------------------------------------------------------------------
+#include <mutex>
+#include <stdio.h>
+
+namespace cgs {
+
+constexpr int64_t kNoAllocMaxTiles = 65536;
+static __device__ __align__(256) float g_fwd_scratch[kNoAllocMaxTiles * kPartials];
+
+// Device address of g_fwd_scratch on the current device.  In host code the array's
+// name is only a host-side stand-in, so the address is queried with
+// cudaGetSymbolAddress once per device (with that device current) and cached.
+static float *noalloc_scratch()
+{
+    static std::mutex mu;
+    static float *ptr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_fwd_scratch);
+        if (e != cudaSuccess) {
+            fprintf(stderr, "libcgs: cudaGetSymbolAddress(scratch) failed: %s\n", cudaGetErrorString(e));
+            return nullptr;
+        }
+        ptr[dev] = static_cast<float *>(p);
+    }
+    return ptr[dev];
+}
+
+}  // namespace cgs
+
+extern "C" int cgs_render_fwd_noalloc(const float *rec, const uint32_t *vals, const uint32_t *ranges,
+                                      const uint32_t *tile_order, int32_t V, const cgs_config *cfg,
+                                      const float *view_weight, const float *tgt_rgb, const float *tgt_depth,
+                                      float *img, float *depth, float *t_final, uint32_t *last, float *loss_view,
+                                      int32_t *depth_count, int32_t *status_dev, void *stream)
+{
+    using namespace cgs;
+    if (!rec || !vals || !ranges || !img || !depth || !t_final || !last || !cfg) return CGS_ERR_ARG;
+    if (cfg->width < 1 || cfg->height < 1 || cfg->width > (1 << 16) || cfg->height > (1 << 16)) return CGS_ERR_ARG;
+    if (cfg->tile != 8 && cfg->tile != 16 && cfg->tile != 32) return CGS_ERR_ARG;
+    if (cfg->batch_depth != 32 && cfg->batch_depth != 64 && cfg->batch_depth != 128 && cfg->batch_depth != 256)
+        return CGS_ERR_ARG;
+    if (V < 1 || ((uintptr_t)rec & 15) != 0) return CGS_ERR_ARG;
+    if (tgt_depth && !tgt_rgb) return CGS_ERR_ARG;
+    if (tgt_rgb && (!loss_view || !depth_count)) return CGS_ERR_ARG;
+    const Grid g = make_grid(*cfg);
+    if (g.Tv * V > kNoAllocMaxTiles) {
+        fprintf(stderr, "libcgs: cgs_render_fwd_noalloc: %lld tiles exceed the built-in maximum of %lld\n",
+                (long long)(g.Tv * V), (long long)kNoAllocMaxTiles);
+        return CGS_ERR_WORKSPACE;
+    }
+    float *scratch = noalloc_scratch();
+    if (!scratch) return CGS_ERR_CUDA;
+    RasterFwdArgs a;
+    a.rec = reinterpret_cast<const float4 *>(rec);
+    a.vals = vals;
+    a.ranges = ranges;
+    a.order = tile_order;
+    a.g = g;
+    a.V = V;
+    a.bg0 = cfg->bg[0];
+    a.bg1 = cfg->bg[1];
+    a.bg2 = cfg->bg[2];
+    a.tgt_rgb = tgt_rgb;
+    a.tgt_depth = tgt_depth;
+    a.img = img;
+    a.depth = depth;
+    a.tfin = t_final;
+    a.last = last;
+    a.partials = scratch;   // every entry the reduction reads is written first: nothing to clear
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = raster_fwd(a, cfg->tile, cfg->batch_depth, s);
+    if (e == cudaSuccess && tgt_rgb)
+        e = loss_reduce(a.partials, g, V, view_weight, cfg->lambda_depth, loss_view, depth_count, status_dev, s);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "libcgs: CUDA error: %s\n", cudaGetErrorString(e));
+        return CGS_ERR_CUDA;
+    }
+    return CGS_OK;
+}
