@@ -116,37 +116,52 @@ k_count_agg(const float4 *__restrict__ rec, int64_t n, Grid g, uint32_t *__restr
 }
 
 // Single-block exclusive scan of the per-tile counts; writes ranges (clamped to the
-// capacity), the total instance count and the capacity status.
+// capacity), the total instance count and the capacity status.  Each of the 32 warps
+// owns a contiguous chunk and walks it 32 entries at a time (coalesced loads, warp
+// shuffle scans); a first pass forms the chunk totals.
+__device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long x)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, x, off);
+        if (lane >= off) x += y;
+    }
+    return x;
+}
+
 __global__ void __launch_bounds__(1024)
 k_scan(uint32_t *__restrict__ count, int64_t Ttot, int64_t capacity, uint32_t *__restrict__ ranges,
        int64_t *__restrict__ n_inst, int32_t *__restrict__ status)
 {
-    __shared__ unsigned long long part[1024];
-    const int64_t per = (Ttot + blockDim.x - 1) / blockDim.x;
-    const int64_t lo = threadIdx.x * per, hi = min(Ttot, lo + per);
+    __shared__ unsigned long long wtot[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t per = (Ttot + 31) / 32;
+    const int64_t lo = (int64_t)w * per, hi = min(Ttot, lo + per);
     unsigned long long s = 0;
-    for (int64_t t = lo; t < hi; t++) s += count[t];
-    part[threadIdx.x] = s;
+    for (int64_t t = lo + lane; t < hi; t += 32) s += count[t];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+    if (lane == 0) wtot[w] = s;
     __syncthreads();
-    // Hillis-Steele inclusive scan of the 1024 partial sums
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        unsigned long long x = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
-        __syncthreads();
-        part[threadIdx.x] += x;
-        __syncthreads();
+    unsigned long long run = 0, total = 0;
+    for (int i = 0; i < 32; i++) {
+        run += (i < w) ? wtot[i] : 0ull;
+        total += wtot[i];
     }
-    unsigned long long run = threadIdx.x ? part[threadIdx.x - 1] : 0ull;
     const unsigned long long cap = (unsigned long long)capacity;
-    for (int64_t t = lo; t < hi; t++) {
-        unsigned long long c = count[t];
-        unsigned long long st = run, en = run + c;
-        count[t] = (uint32_t)min(st, cap);      // bucket start (clamped) for the scatter
-        ranges[2 * t] = (uint32_t)min(st, cap);
-        ranges[2 * t + 1] = (uint32_t)min(en, cap);
-        run = en;
+    for (int64_t base = lo; base < hi; base += 32) {
+        const int64_t t = base + lane;
+        const unsigned long long c = t < hi ? count[t] : 0ull;
+        const unsigned long long incl = warp_incl_scan(c);
+        const unsigned long long st = run + incl - c, en = run + incl;
+        if (t < hi) {
+            count[t] = (uint32_t)min(st, cap);      // bucket start (clamped) for the scatter
+            ranges[2 * t] = (uint32_t)min(st, cap);
+            ranges[2 * t + 1] = (uint32_t)min(en, cap);
+        }
+        run += __shfl_sync(kFull, incl, 31);
     }
-    if (threadIdx.x == blockDim.x - 1) {
-        unsigned long long total = part[blockDim.x - 1];
+    if (threadIdx.x == 0) {
         *n_inst = (int64_t)total;
         count[Ttot] = (uint32_t)min(total, cap);
         if (total > cap) set_status(status, CGS_ERR_CAPACITY);
