@@ -93,10 +93,17 @@ __device__ __forceinline__ int block_compact(bool keep, int *wcnt, int &total)
     return pre;
 }
 
-// Pixels per thread in the raster kernels: a thread owns PPT vertically adjacent pixels,
+// Pixels per thread in the raster kernels: a thread owns kPPT vertically adjacent pixels,
 // so the staged splat is read from shared memory once for PPT pixels and the backward's
 // per-(warp, splat) reduction covers 32*PPT pixels.
-constexpr int kPPT = 2;
+constexpr int kPPT = 4;
+
+// Pixels per thread for tile edge B: kPPT, but at least one full warp per tile.
+template <int B>
+__host__ __device__ constexpr int ppt_for()
+{
+    return (B * B / kPPT >= 32) ? kPPT : (B * B / 32);
+}
 
 // Staged splat, derived exactly from its record (negation and scaling by 1/2 are exact):
 //   s0 = (u, v, -A/2, -B), s1 = (-C/2, opacity, depth, tau), s2 = (r, g, b, -)

@@ -57,9 +57,10 @@ __device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane)
 }
 
 template <int B, int BD>
-__global__ void __launch_bounds__(B *B / kPPT) k_render_bwd(RasterBwdArgs a)
+__global__ void __launch_bounds__(B *B / ppt_for<B>()) k_render_bwd(RasterBwdArgs a)
 {
-    constexpr int NT = B * B / kPPT;
+    constexpr int PPT = ppt_for<B>();
+    constexpr int NT = B * B / PPT;
     constexpr int NW = NT / 32;
     __shared__ float4 s0[BD], s1[BD], s2[BD];
     __shared__ uint32_t sslot[BD], spos[BD];
@@ -70,26 +71,25 @@ __global__ void __launch_bounds__(B *B / kPPT) k_render_bwd(RasterBwdArgs a)
     item_tile(a.order, a.g, tile, view, tx, ty);
     const int lane = threadIdx.x & 31;
     const int px = tx * B + (int)(threadIdx.x % B);
-    const int py0 = ty * B + (int)(threadIdx.x / B) * kPPT;
+    const int py0 = ty * B + (int)(threadIdx.x / B) * PPT;
     const float fx = (float)px;
     const uint32_t start = a.ranges[2 * tile];
     const uint32_t len = a.ranges[2 * tile + 1] - start;
     const size_t HW = (size_t)a.g.W * a.g.H;
 
     // per-pixel state
-    float fy[kPPT], T[kPPT], gI0[kPPT], gI1[kPPT], gI2[kPPT], gD[kPPT], bgdot[kPPT];
-    float acc0[kPPT], acc1[kPPT], acc2[kPPT], accD[kPPT], la[kPPT], lc0[kPPT], lc1[kPPT], lc2[kPPT], lz[kPPT];
-    uint32_t lst[kPPT];
+    float fy[PPT], T[PPT], gI0[PPT], gI1[PPT], gI2[PPT], gD[PPT], bgdot[PPT];
+    float acc0[PPT], acc1[PPT], acc2[PPT], accD[PPT];
+    uint32_t lst[PPT];
     uint32_t m = 0;
 #pragma unroll
-    for (int p = 0; p < kPPT; p++) {
+    for (int p = 0; p < PPT; p++) {
         const int py = py0 + p;
         fy[p] = (float)py;
         lst[p] = 0;
         T[p] = 1.f;
         gI0[p] = gI1[p] = gI2[p] = gD[p] = bgdot[p] = 0.f;
         acc0[p] = acc1[p] = acc2[p] = accD[p] = 0.f;
-        la[p] = lc0[p] = lc1[p] = lc2[p] = lz[p] = 0.f;
         if (!(px < a.g.W && py < a.g.H)) continue;
         const size_t q = (size_t)py * a.g.W + px;
         const size_t pix = (size_t)view * HW + q;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(B *B / kPPT) k_render_bwd(RasterBwdArgs a)
             for (int k = 0; k < 16; k++) v[k] = 0.f;
             bool contrib = false;
 #pragma unroll
-            for (int p = 0; p < kPPT; p++) {
+            for (int p = 0; p < PPT; p++) {
                 if (!(pos < lst[p])) continue;
                 const float dy = __fsub_rn(q0.y, fy[p]);
                 const float power = staged_power(q0, q1.x, dx, dy);
@@ -182,23 +182,20 @@ __global__ void __launch_bounds__(B *B / kPPT) k_render_bwd(RasterBwdArgs a)
                 const float4 q2 = s2[j];
                 const float inv_om = __fdividef(1.f, __fsub_rn(1.f, alpha));
                 T[p] = T[p] * inv_om;                             // transmittance before splat j
-                acc0[p] = fmaf(la[p], lc0[p] - acc0[p], acc0[p]);  // colour behind splat j
-                acc1[p] = fmaf(la[p], lc1[p] - acc1[p], acc1[p]);
-                acc2[p] = fmaf(la[p], lc2[p] - acc2[p], acc2[p]);
-                accD[p] = fmaf(la[p], lz[p] - accD[p], accD[p]);
-                la[p] = alpha;
-                lc0[p] = q2.x;
-                lc1[p] = q2.y;
-                lc2[p] = q2.z;
-                lz[p] = q1.z;
                 const float wT = alpha * T[p];
                 v[8] += wT * gI0[p];
                 v[9] += wT * gI1[p];
                 v[10] += wT * gI2[p];
                 v[6] += wT * gD[p];
+                // acc = colour (and depth) accumulated behind splat j, as seen just after it
                 float dLda = (q2.x - acc0[p]) * gI0[p] + (q2.y - acc1[p]) * gI1[p] + (q2.z - acc2[p]) * gI2[p] +
                              (q1.z - accD[p]) * gD[p];
                 dLda = dLda * T[p] - bgdot[p] * inv_om;
+                // fold splat j in for the splats in front of it: acc <- a c + (1 - a) acc
+                acc0[p] = fmaf(alpha, q2.x - acc0[p], acc0[p]);
+                acc1[p] = fmaf(alpha, q2.y - acc1[p], acc1[p]);
+                acc2[p] = fmaf(alpha, q2.z - acc2[p], acc2[p]);
+                accD[p] = fmaf(alpha, q1.z - accD[p], accD[p]);
                 if (!(araw > kAlphaMax)) {
                     // dalpha/dpower = alpha, dalpha/dopacity = G.  Raw moments of
                     // dp = dL/dpower are summed here; the conic / centre gradients are
@@ -213,7 +210,27 @@ __global__ void __launch_bounds__(B *B / kPPT) k_render_bwd(RasterBwdArgs a)
                     v[4] += dpy * dy;        // sum dp dy^2
                 }
             }
-            if (__any_sync(kFull, contrib)) {
+            const unsigned who = __ballot_sync(kFull, contrib);
+            if (who == 0u) continue;
+            if ((who & (who - 1u)) == 0u) {
+                // a single contributing lane adds its sums directly
+                if (contrib) {
+                    float *g = a.sgrad + (size_t)sslot[j] * 12;
+                    const float hA = s0[j].z, nB = s0[j].w, hC = s1[j].x;
+                    atomicAdd(g + 0, 2.f * hA * v[0] + nB * v[1]);
+                    atomicAdd(g + 1, 2.f * hC * v[1] + nB * v[0]);
+                    atomicAdd(g + 2, -0.5f * v[2]);
+                    atomicAdd(g + 3, -v[3]);
+                    atomicAdd(g + 4, -0.5f * v[4]);
+                    atomicAdd(g + 5, v[5]);
+                    atomicAdd(g + 6, v[6]);
+                    atomicAdd(g + 8, v[8]);
+                    atomicAdd(g + 9, v[9]);
+                    atomicAdd(g + 10, v[10]);
+                }
+                continue;
+            }
+            {
                 float sum = warp_reduce_scatter16(v, lane);
                 const int f = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
                 // fields 0 and 1 sit in lanes that differ in bit 1: exchange the two first moments
@@ -238,7 +255,7 @@ template <int B, int BD>
 static cudaError_t launch_bwd(const RasterBwdArgs &a, cudaStream_t s)
 {
     const int64_t items = a.g.Tv * a.V;
-    k_render_bwd<B, BD><<<(unsigned)items, B * B / kPPT, 0, s>>>(a);
+    k_render_bwd<B, BD><<<(unsigned)items, B * B / ppt_for<B>(), 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -13,9 +13,10 @@
 namespace cgs {
 
 template <int B, int BD>
-__global__ void __launch_bounds__(B *B / kPPT) k_render_fwd(RasterFwdArgs a)
+__global__ void __launch_bounds__(B *B / ppt_for<B>()) k_render_fwd(RasterFwdArgs a)
 {
-    constexpr int NT = B * B / kPPT;
+    constexpr int PPT = ppt_for<B>();
+    constexpr int NT = B * B / PPT;
     constexpr int NW = NT / 32;
     __shared__ float4 s0[BD], s1[BD], s2[BD];
     __shared__ uint32_t spos[BD];
@@ -25,19 +26,19 @@ __global__ void __launch_bounds__(B *B / kPPT) k_render_fwd(RasterFwdArgs a)
     int view, tx, ty;
     item_tile(a.order, a.g, tile, view, tx, ty);
     const int px = tx * B + (int)(threadIdx.x % B);
-    const int py0 = ty * B + (int)(threadIdx.x / B) * kPPT;
+    const int py0 = ty * B + (int)(threadIdx.x / B) * PPT;
     const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
     const float fx = (float)px;
     // pixel-centre box of the tile (clipped to the image)
     const float bx0 = (float)(tx * B), bx1 = (float)(min(tx * B + B, a.g.W) - 1);
     const float by0 = (float)(ty * B), by1 = (float)(min(ty * B + B, a.g.H) - 1);
 
-    float fy[kPPT], T[kPPT], C0[kPPT], C1[kPPT], C2[kPPT], D[kPPT];
-    uint32_t lst[kPPT];
-    bool done[kPPT];
+    float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
+    uint32_t lst[PPT];
+    bool done[PPT];
     bool tdone = true;
 #pragma unroll
-    for (int p = 0; p < kPPT; p++) {
+    for (int p = 0; p < PPT; p++) {
         fy[p] = (float)(py0 + p);
         T[p] = 1.f;
         C0[p] = C1[p] = C2[p] = D[p] = 0.f;
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(B *B / kPPT) k_render_fwd(RasterFwdArgs a)
                 const float dx = __fsub_rn(q0.x, fx);
                 bool all = true;
 #pragma unroll
-                for (int p = 0; p < kPPT; p++) {
+                for (int p = 0; p < PPT; p++) {
                     if (done[p]) continue;
                     n_eval++;
                     const float dy = __fsub_rn(q0.y, fy[p]);
@@ -107,14 +108,14 @@ __global__ void __launch_bounds__(B *B / kPPT) k_render_fwd(RasterFwdArgs a)
             }
             tdone = true;
 #pragma unroll
-            for (int p = 0; p < kPPT; p++) tdone = tdone && done[p];
+            for (int p = 0; p < PPT; p++) tdone = tdone && done[p];
         }
     }
 
     float l_rgb = 0.f, l_d = 0.f, c_d = 0.f;
     const size_t HW = (size_t)a.g.W * a.g.H;
 #pragma unroll
-    for (int p = 0; p < kPPT; p++) {
+    for (int p = 0; p < PPT; p++) {
         const int py = py0 + p;
         if (!(px < a.g.W && py < a.g.H)) continue;
         const size_t q = (size_t)py * a.g.W + px;
@@ -206,7 +207,7 @@ template <int B, int BD>
 static cudaError_t launch_fwd(const RasterFwdArgs &a, cudaStream_t s)
 {
     const int64_t items = a.g.Tv * a.V;
-    k_render_fwd<B, BD><<<(unsigned)items, B * B / kPPT, 0, s>>>(a);
+    k_render_fwd<B, BD><<<(unsigned)items, B * B / ppt_for<B>(), 0, s>>>(a);
     return cudaGetLastError();
 }
 
