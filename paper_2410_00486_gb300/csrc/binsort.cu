@@ -276,6 +276,164 @@ __device__ __forceinline__ uint32_t next_pow2(uint32_t x)
     return x <= 1 ? 1u : 1u << (32 - __clz(x - 1));
 }
 
+// Per-tile stable LSD radix sort in shared memory (lists of up to kSmallCap keys).
+// The key is (depth bits << 32 | slot) and is unique in a tile, so sorting by the depth
+// bits (8-bit digits; a pass whose digit is the same for every key of the tile is
+// skipped) and then ordering each run of equal depths by slot gives exactly the
+// (depth, slot) order.  Stability: warp w owns a contiguous segment of the list and
+// walks it 32 keys at a time; a ballot multisplit ranks equal digits within a step, and
+// per-warp digit histograms scanned digit-major give each (digit, warp) its start.
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+
+// Lanes of the warp whose 8-bit digit equals this lane's (restricted to `valid` lanes),
+// from eight ballots, one per digit bit (a ballot-based multisplit: __match_any_sync
+// runs on a low-throughput pipe).
+__device__ __forceinline__ unsigned same_digit_lanes(uint32_t d, unsigned valid)
+{
+    unsigned peers = valid;
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        const bool bit = (d >> b) & 1u;
+        const unsigned bal = __ballot_sync(kFull, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
+
+__device__ __forceinline__ uint32_t block_excl_scan256(uint32_t x, uint32_t *wsum)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    uint32_t pre = 0;
+    for (int i = 0; i < w; i++) pre += wsum[i];
+    __syncthreads();
+    return pre + incl - x;
+}
+
+__global__ void __launch_bounds__(kRsThreads)
+k_sort_tiles(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+             uint32_t *__restrict__ big, uint32_t *__restrict__ nbig)
+{
+    __shared__ uint64_t bufA[kSmallCap], bufB[kSmallCap];
+    __shared__ uint32_t hist[kRsWarps][256];
+    __shared__ uint32_t wsum[kRsWarps], wor[kRsWarps], wand[kRsWarps];
+    const int64_t t = blockIdx.x;
+    const uint32_t st = ranges[2 * t], en = ranges[2 * t + 1];
+    const uint32_t len = en - st;
+    if (len == 0) return;
+    if (len > (uint32_t)kSmallCap) {
+        if (threadIdx.x == 0) big[atomicAdd(nbig, 1u)] = (uint32_t)t;
+        return;
+    }
+    if (len == 1) {
+        if (threadIdx.x == 0) vals[st] = (uint32_t)keys[st];
+        return;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // load, and find the depth bits that vary across the tile
+    uint32_t bor = 0u, band = ~0u;
+    for (uint32_t i = threadIdx.x; i < len; i += kRsThreads) {
+        const uint64_t k = keys[st + i];
+        bufA[i] = k;
+        const uint32_t d = (uint32_t)(k >> 32);
+        bor |= d;
+        band &= d;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        bor |= __shfl_xor_sync(kFull, bor, off);
+        band &= __shfl_xor_sync(kFull, band, off);
+    }
+    if (lane == 0) {
+        wor[w] = bor;
+        wand[w] = band;
+    }
+    __syncthreads();
+    uint32_t vary = 0u, all_and = ~0u;
+    for (int i = 0; i < kRsWarps; i++) {
+        vary |= wor[i];
+        all_and &= wand[i];
+    }
+    vary ^= all_and;
+    uint64_t *src = bufA, *dst = bufB;
+    const uint32_t per = (len + kRsWarps - 1) / kRsWarps;
+    const uint32_t seg0 = min(len, (uint32_t)w * per), seg1 = min(len, seg0 + per);
+    for (int shift = 0; shift < 32; shift += 8) {
+        if (((vary >> shift) & 0xffu) == 0u) continue;      // block-uniform
+        for (int i = lane; i < 256; i += 32) hist[w][i] = 0u;
+        __syncwarp();
+        for (uint32_t c = seg0; c < seg1; c += 32) {
+            const uint32_t e = c + lane;
+            const bool valid = e < seg1;
+            const uint32_t d = valid ? ((uint32_t)(src[e] >> (32 + shift)) & 0xffu) : 0u;
+            const unsigned peers = same_digit_lanes(d, __ballot_sync(kFull, valid));
+            if (valid && lane == __ffs(peers) - 1) hist[w][d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {   // start of each (digit, warp) run: digit-major exclusive scan
+            const uint32_t dg = threadIdx.x;       // 256 threads = 256 digits
+            uint32_t cnts[kRsWarps], tot = 0u;
+#pragma unroll
+            for (int i = 0; i < kRsWarps; i++) {
+                cnts[i] = hist[i][dg];
+                tot += cnts[i];
+            }
+            uint32_t off = block_excl_scan256(tot, wsum);
+#pragma unroll
+            for (int i = 0; i < kRsWarps; i++) {
+                hist[i][dg] = off;
+                off += cnts[i];
+            }
+        }
+        __syncthreads();
+        for (uint32_t c = seg0; c < seg1; c += 32) {
+            const uint32_t e = c + lane;
+            const bool valid = e < seg1;
+            const uint64_t k = valid ? src[e] : 0ull;
+            const uint32_t d = valid ? ((uint32_t)(k >> (32 + shift)) & 0xffu) : 0u;
+            const unsigned peers = same_digit_lanes(d, __ballot_sync(kFull, valid));
+            const uint32_t base = valid ? hist[w][d] : 0u;
+            __syncwarp();
+            if (valid) {
+                dst[base + __popc(peers & ((1u << lane) - 1u))] = k;
+                if (lane == __ffs(peers) - 1) hist[w][d] = base + __popc(peers);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        uint64_t *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    // runs of equal depth: order by slot (rare; insertion sort by the run's first thread)
+    for (uint32_t i = threadIdx.x; i + 1 < len; i += kRsThreads) {
+        const uint32_t di = (uint32_t)(src[i] >> 32);
+        const bool starts = (i == 0 || (uint32_t)(src[i - 1] >> 32) != di) && (uint32_t)(src[i + 1] >> 32) == di;
+        if (!starts) continue;
+        uint32_t e = i + 1;
+        while (e < len && (uint32_t)(src[e] >> 32) == di) e++;
+        for (uint32_t a = i + 1; a < e; a++) {
+            const uint64_t k = src[a];
+            uint32_t b = a;
+            while (b > i && src[b - 1] > k) {
+                src[b] = src[b - 1];
+                b--;
+            }
+            src[b] = k;
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < len; i += kRsThreads) vals[st + i] = (uint32_t)src[i];
+}
+
 __global__ void __launch_bounds__(kSmallThreads)
 k_sort_small(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
              uint32_t *__restrict__ big, uint32_t *__restrict__ nbig)
@@ -403,7 +561,7 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
         k_scatter_agg<<<agrid, kAggThreads, hist_bytes, s>>>(r4, n, g, w.count, w.cursor, w.keys, capacity);
     else
         k_scatter<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count, w.cursor, w.keys, capacity);
-    k_sort_small<<<(unsigned)Ttot, kSmallThreads, 0, s>>>(ranges, w.keys, vals, w.big, w.nbig);
+    k_sort_tiles<<<(unsigned)Ttot, kRsThreads, 0, s>>>(ranges, w.keys, vals, w.big, w.nbig);
     const size_t big_smem = sizeof(uint64_t) * kBigCap;
     e = cudaFuncSetAttribute(k_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem);
     if (e != cudaSuccess) return e;

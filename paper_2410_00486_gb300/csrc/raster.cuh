@@ -93,16 +93,19 @@ __device__ __forceinline__ int block_compact(bool keep, int *wcnt, int &total)
     return pre;
 }
 
-// Pixels per thread in the raster kernels: a thread owns kPPT vertically adjacent pixels,
+// Pixels per thread in the raster kernels: a thread owns several vertically adjacent pixels,
 // so the staged splat is read from shared memory once for PPT pixels and the backward's
 // per-(warp, splat) reduction covers 32*PPT pixels.
-constexpr int kPPT = 4;
+// The forward keeps two (its per-thread state is small and occupancy pays), the
+// backward four (fewer warp reductions per pixel).
+constexpr int kPPTFwd = 2;
+constexpr int kPPTBwd = 4;
 
-// Pixels per thread for tile edge B: kPPT, but at least one full warp per tile.
-template <int B>
+// Pixels per thread for tile edge B: P, but at least one full warp per tile.
+template <int B, int P>
 __host__ __device__ constexpr int ppt_for()
 {
-    return (B * B / kPPT >= 32) ? kPPT : (B * B / 32);
+    return (B * B / P >= 32) ? P : (B * B / 32);
 }
 
 // Staged splat, derived exactly from its record (negation and scaling by 1/2 are exact):

@@ -57,9 +57,9 @@ __device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane)
 }
 
 template <int B, int BD>
-__global__ void __launch_bounds__(B *B / ppt_for<B>()) k_render_bwd(RasterBwdArgs a)
+__global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>()) k_render_bwd(RasterBwdArgs a)
 {
-    constexpr int PPT = ppt_for<B>();
+    constexpr int PPT = ppt_for<B, kPPTBwd>();
     constexpr int NT = B * B / PPT;
     constexpr int NW = NT / 32;
     __shared__ float4 s0[BD], s1[BD], s2[BD];
@@ -255,7 +255,7 @@ template <int B, int BD>
 static cudaError_t launch_bwd(const RasterBwdArgs &a, cudaStream_t s)
 {
     const int64_t items = a.g.Tv * a.V;
-    k_render_bwd<B, BD><<<(unsigned)items, B * B / ppt_for<B>(), 0, s>>>(a);
+    k_render_bwd<B, BD><<<(unsigned)items, B * B / ppt_for<B, kPPTBwd>(), 0, s>>>(a);
     return cudaGetLastError();
 }
 

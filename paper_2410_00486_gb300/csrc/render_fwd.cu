@@ -13,9 +13,9 @@
 namespace cgs {
 
 template <int B, int BD>
-__global__ void __launch_bounds__(B *B / ppt_for<B>()) k_render_fwd(RasterFwdArgs a)
+__global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>()) k_render_fwd(RasterFwdArgs a)
 {
-    constexpr int PPT = ppt_for<B>();
+    constexpr int PPT = ppt_for<B, kPPTFwd>();
     constexpr int NT = B * B / PPT;
     constexpr int NW = NT / 32;
     __shared__ float4 s0[BD], s1[BD], s2[BD];
@@ -46,7 +46,9 @@ __global__ void __launch_bounds__(B *B / ppt_for<B>()) k_render_fwd(RasterFwdArg
         done[p] = !(px < a.g.W && py0 + p < a.g.H);
         tdone = tdone && done[p];
     }
-    uint32_t n_eval = 0, n_blend = 0;
+    uint32_t n_eval = 0, n_blend = 0, active = 0;
+#pragma unroll
+    for (int p = 0; p < PPT; p++) active += done[p] ? 0u : 1u;
     for (uint32_t base = start; base < end; base += BD) {
         if (__syncthreads_count(!tdone) == 0) break;
         // stage the batch, keeping (in list order) only splats that can touch the tile
@@ -79,19 +81,18 @@ __global__ void __launch_bounds__(B *B / ppt_for<B>()) k_render_fwd(RasterFwdArg
                 const float4 q0 = s0[j];
                 const float4 q1 = s1[j];
                 const float dx = __fsub_rn(q0.x, fx);
-                bool all = true;
+                n_eval += active;
 #pragma unroll
                 for (int p = 0; p < PPT; p++) {
                     if (done[p]) continue;
-                    n_eval++;
                     const float dy = __fsub_rn(q0.y, fy[p]);
                     const float power = staged_power(q0, q1.x, dx, dy);
-                    all = false;
                     if (power > 0.f || power < q1.w) continue;
                     const float alpha = fminf(kAlphaMax, __fmul_rn(q1.y, __expf(power)));
                     const float testT = __fmul_rn(T[p], __fsub_rn(1.f, alpha));
                     if (testT < kTMin) {
                         done[p] = true;
+                        active--;
                         continue;
                     }
                     const float wgt = __fmul_rn(alpha, T[p]);
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B>()) k_render_fwd(RasterFwdArg
                     lst[p] = spos[j] + 1u;
                     n_blend++;
                 }
-                if (all) break;
+                if (active == 0u) break;
             }
             tdone = true;
 #pragma unroll
@@ -207,7 +208,7 @@ template <int B, int BD>
 static cudaError_t launch_fwd(const RasterFwdArgs &a, cudaStream_t s)
 {
     const int64_t items = a.g.Tv * a.V;
-    k_render_fwd<B, BD><<<(unsigned)items, B * B / ppt_for<B>(), 0, s>>>(a);
+    k_render_fwd<B, BD><<<(unsigned)items, B * B / ppt_for<B, kPPTFwd>(), 0, s>>>(a);
     return cudaGetLastError();
 }
 
