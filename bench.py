@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stages", action="store_true")
+    ap.add_argument("--no-splat", action="store_true", help="skip the splat-wise backward head-to-head")
     return ap.parse_args()
 
 
@@ -330,6 +331,12 @@ def main():
         del pv, g
         torch.cuda.empty_cache()
 
+    # --- head to head: the paper's splat-wise backward (Fig. 4a) in the same iteration
+    splat = None
+    if not args.no_splat and tile in (8, 16):
+        splat = splat_head_to_head(MappingWindow, params_t, sc, tile, bd, cams, tgt_rgb, tgt_d, win.capacity,
+                                   max(3, args.steps // 4), args.warmup, value / world)
+
     # --- stage breakdown (eager, CUDA events on the launching stream)
     stages = None
     work = None
@@ -362,6 +369,7 @@ def main():
             "config": workload_config(sc, extra),
             "view_iters_per_s": value * V,
             "per_view_form": per_view,
+            "splat_backward": splat,
             "e2e": {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
             if e2e else None,
             "gpu_launches": gpu_launches,
@@ -373,6 +381,52 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def splat_head_to_head(MappingWindow, params_t, sc, tile, bd, cams, tgt_rgb, tgt_d, capacity, k, warmup,
+                       pixel_value):
+    """Window iterations/s with the splat-wise backward (forward saving per-pixel states every
+    32 splats), plus its forward and backward stage times."""
+    import torch
+    from paper_2410_00486_gb300 import _native as N
+    w = MappingWindow(params_t.clone(), sc.n, sc.sh_degree, sc.width, sc.height, sc.views, tile=tile,
+                      batch_depth=bd, capacity=capacity, backward="splat")
+    w.set_window(cams, tgt_rgb, tgt_d)
+    w.capture()
+    for _ in range(warmup):
+        w.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(k):
+        w.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    st = w.read_status()
+    if st[0] != 0:
+        raise SystemExit(f"device status (splat-wise backward): {st}")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    N.cgs_preprocess(w.params, w.n, w.cams, w.V, w.cfg, w.rec, w.slot_grad, w.status)
+    N.cgs_bin_sort(w.rec, w.n, w.V, w.cfg, w.bin_ws, w.capacity, w.vals, w.ranges, w.order, w.n_inst, w.status)
+    ev[0].record()
+    N.cgs_render_fwd_ckpt(w.rec, w.vals, w.ranges, w.order, w.V, w.cfg, w.view_weight, w.tgt_rgb, w.tgt_depth,
+                          w.img, w.depth, w.t_final, w.last, w.loss_view, w.depth_count, w.fwd_ws, w.ckpt,
+                          w.max_buckets, w.bucket_start, w.status)
+    ev[1].record()
+    N.cgs_raster_bwd_splat(w.rec, w.vals, w.ranges, w.order, w.V, w.cfg, w.view_weight, w.img, w.depth,
+                           w.t_final, w.last, w.tgt_rgb, w.tgt_depth, w.depth_count, None, None, w.ckpt,
+                           w.max_buckets, w.bucket_start, w.slot_grad, w.status)
+    ev[2].record()
+    torch.cuda.synchronize()
+    out = {"value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "steps": k,
+           "render_fwd_ckpt_ms": round(ev[0].elapsed_time(ev[1]), 4),
+           "raster_bwd_splat_ms": round(ev[1].elapsed_time(ev[2]), 4),
+           "checkpoint_buckets": int(w.bucket_start[-1].item()),
+           "pixel_wise_over_splat_wise": pixel_value / (1e3 / ms)}
+    del w
+    torch.cuda.empty_cache()
+    return out
 
 
 def stage_breakdown(win, N, reps=5):

@@ -213,6 +213,37 @@ int cgs_raster_bwd(const float *rec, const uint32_t *vals, const uint32_t *range
                    const float *dl_ddepth, float *slot_grad, int32_t *status_dev, void *stream);
 
 /*
+ * Splat-wise backward (Sec. III-C.1 and Fig. 4a: the paper's backward).  The forward
+ * saves every pixel's state (transmittance, accumulated colour, accumulated depth)
+ * before list positions 32, 64, ... of its tile; the backward gives each warp a bucket
+ * of 32 consecutive splats (one per lane), passes pixel states from lane to lane with
+ * shuffles, and adds each splat's gradient once per tile (no per-pixel reduction).
+ * Results equal cgs_raster_bwd's up to float summation order.
+ *   cgs_ckpt_bytes(max_buckets, cfg) = max_buckets * tile^2 * 20 bytes of checkpoints;
+ *     a window needs sum over tiles of ceil(len / 32) buckets <= n_inst / 32 + tiles.
+ *   cgs_render_fwd_ckpt: cgs_render_fwd plus the checkpoints.
+ *     ckpt          device out, 16-byte aligned, cgs_ckpt_bytes(max_buckets, cfg) bytes
+ *     bucket_start  device out, uint32[V * tiles_per_view + 1]: first bucket of each tile
+ *     more buckets than max_buckets set CGS_ERR_CAPACITY (checkpoints past it are dropped)
+ *   cgs_raster_bwd_splat: cgs_raster_bwd reading those checkpoints (tile 8 or 16).
+ */
+size_t cgs_ckpt_bytes(int64_t max_buckets, const cgs_config *cfg);
+int cgs_render_fwd_ckpt(const float *rec, const uint32_t *vals, const uint32_t *ranges,
+                        const uint32_t *tile_order, int32_t V, const cgs_config *cfg,
+                        const float *view_weight, const float *tgt_rgb, const float *tgt_depth,
+                        float *img, float *depth, float *t_final, uint32_t *last, float *loss_view,
+                        int32_t *depth_count, void *workspace, size_t workspace_bytes, float *ckpt,
+                        int64_t max_buckets, uint32_t *bucket_start, int32_t *status_dev, void *stream);
+int cgs_raster_bwd_splat(const float *rec, const uint32_t *vals, const uint32_t *ranges,
+                         const uint32_t *tile_order, int32_t V, const cgs_config *cfg,
+                         const float *view_weight, const float *img, const float *depth,
+                         const float *t_final, const uint32_t *last, const float *tgt_rgb,
+                         const float *tgt_depth, const int32_t *depth_count, const float *dl_dimg,
+                         const float *dl_ddepth, const float *ckpt, int64_t max_buckets,
+                         const uint32_t *bucket_start, float *slot_grad, int32_t *status_dev,
+                         void *stream);
+
+/*
  * cgs_preprocess_bwd -- chain rule from the slot gradients of every visible slot
  * back to the parameters (position, log-scale, quaternion, opacity logit, SH),
  * summed over the V views; the derivative of a guard-band-clamped Jacobian entry

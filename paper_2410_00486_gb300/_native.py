@@ -60,6 +60,11 @@ _SIGS = {
                                  c_size_t, _P, _P]),
     "cgs_render_fwd_noalloc": (c_int32, [_P, _P, _P, _P, c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                          _P, _P]),
+    "cgs_ckpt_bytes": (c_size_t, [c_int64, _P]),
+    "cgs_render_fwd_ckpt": (c_int32, [_P, _P, _P, _P, c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                      c_size_t, _P, c_int64, _P, _P, _P]),
+    "cgs_raster_bwd_splat": (c_int32, [_P, _P, _P, _P, c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                       _P, c_int64, _P, _P, _P, _P]),
     "cgs_raster_bwd": (c_int32, [_P, _P, _P, _P, c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                  _P, _P, _P]),
     "cgs_preprocess_bwd": (c_int32, [_P, c_int64, _P, c_int32, _P, _P, _P, _P, c_int32, _P, _P, _P,
@@ -179,6 +184,31 @@ def cgs_render_fwd_noalloc(rec, vals, ranges, tile_order, V, cfg, view_weight, t
         _dev(rec), _dev(vals), _dev(ranges), _dev(tile_order), V, byref(cfg), _dev(view_weight),
         _dev(tgt_rgb), _dev(tgt_depth), _dev(img), _dev(depth), _dev(t_final), _dev(last),
         _dev(loss_view), _dev(depth_count), _dev(status), _stream(stream)))
+
+
+def cgs_ckpt_bytes(max_buckets, cfg) -> int:
+    return lib().cgs_ckpt_bytes(max_buckets, byref(cfg))
+
+
+def cgs_render_fwd_ckpt(rec, vals, ranges, tile_order, V, cfg, view_weight, tgt_rgb, tgt_depth, img, depth,
+                        t_final, last, loss_view, depth_count, workspace, ckpt, max_buckets, bucket_start,
+                        status=None, stream=None):
+    nbytes = workspace.numel() * workspace.element_size()
+    _check("cgs_render_fwd_ckpt", lib().cgs_render_fwd_ckpt(
+        _dev(rec), _dev(vals), _dev(ranges), _dev(tile_order), V, byref(cfg), _dev(view_weight),
+        _dev(tgt_rgb), _dev(tgt_depth), _dev(img), _dev(depth), _dev(t_final), _dev(last),
+        _dev(loss_view), _dev(depth_count), _dev(workspace), nbytes, _dev(ckpt), max_buckets,
+        _dev(bucket_start), _dev(status), _stream(stream)))
+
+
+def cgs_raster_bwd_splat(rec, vals, ranges, tile_order, V, cfg, view_weight, img, depth, t_final, last,
+                         tgt_rgb, tgt_depth, depth_count, dl_dimg, dl_ddepth, ckpt, max_buckets, bucket_start,
+                         slot_grad, status=None, stream=None):
+    _check("cgs_raster_bwd_splat", lib().cgs_raster_bwd_splat(
+        _dev(rec), _dev(vals), _dev(ranges), _dev(tile_order), V, byref(cfg), _dev(view_weight), _dev(img),
+        _dev(depth), _dev(t_final), _dev(last), _dev(tgt_rgb), _dev(tgt_depth), _dev(depth_count),
+        _dev(dl_dimg), _dev(dl_ddepth), _dev(ckpt), max_buckets, _dev(bucket_start), _dev(slot_grad),
+        _dev(status), _stream(stream)))
 
 
 def cgs_raster_bwd(rec, vals, ranges, tile_order, V, cfg, view_weight, img, depth, t_final, last, tgt_rgb,

@@ -19,7 +19,8 @@ INCLUDE = ROOT / "include"
 BUILD = PKG / "_build"
 LIB = BUILD / "libcgs.so"
 
-CUDA_SOURCES = ["preprocess.cu", "binsort.cu", "render_fwd.cu", "render_bwd.cu", "adam.cu", "capi.cu"]
+CUDA_SOURCES = ["preprocess.cu", "binsort.cu", "render_fwd.cu", "render_bwd.cu", "render_bwd_splat.cu", "adam.cu",
+                "capi.cu"]
 CPP_SOURCES = ["sched.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -155,6 +155,10 @@ int cgs_render_fwd(const float *rec, const uint32_t *vals, const uint32_t *range
     a.tfin = t_final;
     a.last = last;
     a.partials = static_cast<float *>(workspace);
+    a.ck4 = nullptr;
+    a.ckD = nullptr;
+    a.bucket_start = nullptr;
+    a.max_buckets = 0;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = raster_fwd(a, cfg->tile, cfg->batch_depth, s);
     if (e == cudaSuccess && tgt_rgb)

@@ -15,7 +15,16 @@ struct RasterFwdArgs {
     float *img, *depth, *tfin;
     uint32_t *last;
     float *partials;   // [Ttot][kPartials], see below
+    // optional checkpoints for the splat-wise backward (null = none): the state of every
+    // pixel before list positions 32, 64, ... of its tile
+    float4 *ck4;                 // [bucket][B*B] (T, C0, C1, C2)
+    float *ckD;                  // [bucket][B*B] depth
+    const uint32_t *bucket_start;  // [Ttot + 1] first bucket of each tile
+    int64_t max_buckets;
 };
+
+// Checkpoint bucket of list positions [32 k, 32 k + 32) of a tile.
+constexpr int kBucket = 32;
 
 // Per-tile partial sums written by the forward: sum |r_rgb|, sum |r_depth| over valid
 // depth pixels, valid depth count, (splat, pixel) pairs evaluated, pairs blended.

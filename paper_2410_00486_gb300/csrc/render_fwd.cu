@@ -12,7 +12,7 @@
 
 namespace cgs {
 
-template <int B, int BD>
+template <int B, int BD, bool CKPT>
 __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>()) k_render_fwd(RasterFwdArgs a)
 {
     constexpr int PPT = ppt_for<B, kPPTFwd>();
@@ -47,6 +47,9 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>()) k_render_fwd(Ras
         tdone = tdone && done[p];
     }
     uint32_t n_eval = 0, n_blend = 0, active = 0;
+    uint32_t next_ck = kBucket;   // next checkpoint boundary (list position)
+    const int64_t ck_base = CKPT ? (int64_t)a.bucket_start[tile] : 0;
+    const int pix0 = (int)(threadIdx.x / B) * PPT * B + (int)(threadIdx.x % B);   // pixel index in the tile
 #pragma unroll
     for (int p = 0; p < PPT; p++) active += done[p] ? 0u : 1u;
     for (uint32_t base = start; base < end; base += BD) {
@@ -78,6 +81,22 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>()) k_render_fwd(Ras
         __syncthreads();
         if (!tdone) {
             for (int j = 0; j < cnt; j++) {
+                if (CKPT) {
+                    // save the state of this thread's pixels at every boundary up to this splat
+                    const uint32_t sp = spos[j];
+                    while (next_ck <= sp) {
+                        const int64_t bk = ck_base + (int64_t)(next_ck / kBucket);
+                        if (bk < a.max_buckets) {
+#pragma unroll
+                            for (int p = 0; p < PPT; p++) {
+                                const int64_t q = bk * (B * B) + pix0 + p * B;
+                                a.ck4[q] = make_float4(T[p], C0[p], C1[p], C2[p]);
+                                a.ckD[q] = D[p];
+                            }
+                        }
+                        next_ck += kBucket;
+                    }
+                }
                 const float4 q0 = s0[j];
                 const float4 q1 = s1[j];
                 const float dx = __fsub_rn(q0.x, fx);
@@ -208,7 +227,10 @@ template <int B, int BD>
 static cudaError_t launch_fwd(const RasterFwdArgs &a, cudaStream_t s)
 {
     const int64_t items = a.g.Tv * a.V;
-    k_render_fwd<B, BD><<<(unsigned)items, B * B / ppt_for<B, kPPTFwd>(), 0, s>>>(a);
+    if (a.ck4)
+        k_render_fwd<B, BD, true><<<(unsigned)items, B * B / ppt_for<B, kPPTFwd>(), 0, s>>>(a);
+    else
+        k_render_fwd<B, BD, false><<<(unsigned)items, B * B / ppt_for<B, kPPTFwd>(), 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -324,6 +346,10 @@ extern "C" int cgs_render_fwd_noalloc(const float *rec, const uint32_t *vals, co
     a.tfin = t_final;
     a.last = last;
     a.partials = scratch;   // every entry the reduction reads is written first: nothing to clear
+    a.ck4 = nullptr;
+    a.ckD = nullptr;
+    a.bucket_start = nullptr;
+    a.max_buckets = 0;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = raster_fwd(a, cfg->tile, cfg->batch_depth, s);
     if (e == cudaSuccess && tgt_rgb)

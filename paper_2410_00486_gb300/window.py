@@ -39,7 +39,7 @@ class MappingWindow:
                  tile: int = 16, batch_depth: int = 64, lr=LR_DEFAULT, lambda_o: float = 0.0,
                  lambda_depth: float = 0.1, bg=(0.0, 0.0, 0.0), near_z: float = 0.2,
                  betas=(0.9, 0.999), eps: float = 1e-15, capacity: int | None = None,
-                 densify_stats: bool = True, tile_order: bool = True):
+                 densify_stats: bool = True, tile_order: bool = True, backward: str = "pixel"):
         if not params.is_cuda or params.dtype != torch.float32:
             raise ValueError("params must be a float32 CUDA tensor")
         dev = params.device
@@ -56,6 +56,9 @@ class MappingWindow:
         self.betas = (float(betas[0]), float(betas[1]))
         self.eps = float(eps)
         self.densify = densify_stats
+        if backward not in ("pixel", "splat"):
+            raise ValueError("backward must be 'pixel' or 'splat'")
+        self.backward_kind = backward
         f32 = dict(dtype=torch.float32, device=dev)
 
         self.params = params.contiguous()
@@ -102,6 +105,12 @@ class MappingWindow:
         self.vals = _u32(max(1, self.capacity), self.device)
         ws = N.cgs_bin_sort_workspace(self.capacity, self.V, self.cfg)
         self.bin_ws = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        if self.backward_kind == "splat":
+            # checkpoints of the splat-wise backward: at most capacity / 32 + tiles buckets
+            self.max_buckets = self.capacity // 32 + self.Ttot
+            nb = N.cgs_ckpt_bytes(self.max_buckets, self.cfg)
+            self.ckpt = torch.empty(nb // 4, dtype=torch.float32, device=self.device)
+            self.bucket_start = _u32(self.Ttot + 1, self.device)
         self._pv = None
         self.graph = None
 
@@ -127,10 +136,17 @@ class MappingWindow:
         N.cgs_preprocess(p, self.n, self.cams, self.V, c, self.rec, self.slot_grad, self.status)
         N.cgs_bin_sort(self.rec, self.n, self.V, c, self.bin_ws, self.capacity, self.vals, self.ranges,
                        self.order, self.n_inst, self.status)
-        N.cgs_render_fwd(self.rec, self.vals, self.ranges, self.order, self.V, c, self.view_weight,
-                         self.tgt_rgb if with_loss else None, self.tgt_depth if with_loss else None,
-                         self.img, self.depth, self.t_final, self.last, self.loss_view, self.depth_count,
-                         self.fwd_ws, self.status)
+        if self.backward_kind == "splat":
+            N.cgs_render_fwd_ckpt(self.rec, self.vals, self.ranges, self.order, self.V, c, self.view_weight,
+                                  self.tgt_rgb if with_loss else None, self.tgt_depth if with_loss else None,
+                                  self.img, self.depth, self.t_final, self.last, self.loss_view,
+                                  self.depth_count, self.fwd_ws, self.ckpt, self.max_buckets,
+                                  self.bucket_start, self.status)
+        else:
+            N.cgs_render_fwd(self.rec, self.vals, self.ranges, self.order, self.V, c, self.view_weight,
+                             self.tgt_rgb if with_loss else None, self.tgt_depth if with_loss else None,
+                             self.img, self.depth, self.t_final, self.last, self.loss_view, self.depth_count,
+                             self.fwd_ws, self.status)
 
     def backward(self, dl_dimg=None, dl_ddepth=None, params: torch.Tensor | None = None,
                  grads_out: torch.Tensor | None = None):
@@ -139,6 +155,15 @@ class MappingWindow:
         d = self.densify and dl_dimg is None
         p = self.params if params is None else params
         g = self.grads if grads_out is None else grads_out
+        if self.backward_kind == "splat":
+            N.cgs_raster_bwd_splat(self.rec, self.vals, self.ranges, self.order, self.V, self.cfg,
+                                   self.view_weight, self.img, self.depth, self.t_final, self.last, self.tgt_rgb,
+                                   self.tgt_depth, self.depth_count, dl_dimg, dl_ddepth, self.ckpt,
+                                   self.max_buckets, self.bucket_start, self.slot_grad, self.status)
+            N.cgs_preprocess_bwd(p, self.n, self.cams, self.V, self.cfg, self.rec, self.slot_grad, g, False,
+                                 self.accum if d else None, self.denom if d else None,
+                                 self.max_r2d if d else None, self.status)
+            return
         N.cgs_render_bwd(p, self.n, self.cams, self.V, self.cfg, self.rec, self.vals, self.ranges,
                          self.order, self.view_weight, self.img, self.depth, self.t_final, self.last,
                          self.tgt_rgb, self.tgt_depth, self.depth_count, dl_dimg, dl_ddepth, self.slot_grad,

@@ -524,3 +524,80 @@ def test_autograd_functions_match_fused_backward():
     (l2 + 0.1 * ld).sum().backward()
     for k, sl in group_slices(sc.n, 3).items():
         assert rel_l2(p2.grad[sl].cpu().numpy(), it["grads"][sl]) < GRAD_REL_TOL, k
+
+
+# ------------------------------------------------- splat-wise backward (Fig. 4a)
+
+@pytest.mark.parametrize("name,bd,tile", [("cfg1", 64, 16), ("cfg3", 128, 16), ("tiny_sh3_3views", 32, 8),
+                                          ("room_sh3_20k", 64, 16), ("path_sh3_3views", 256, 16)])
+def test_splat_backward_matches_oracle(name, bd, tile):
+    """Forward with checkpoints + splat-wise backward against the oracle, on the same float32
+    records (checkpoint buffers sized exactly; tile 8 and 16)."""
+    torch = torch_cuda()
+    N = native()
+    sc, tgt_rgb, tgt_d = scene(name)
+    V, n, H, W = sc.views, sc.n, sc.height, sc.width
+    pre = O.preprocess(sc.params, n, sc.sh_degree, sc.cams, W, H, tile)
+    rec = round32(pre["rec"])
+    ranges, vals = O.bin_lists(rec[:, 0], rec[:, 1], rec[:, 9], pre["radius"], V, n, W, H, tile)
+    fw = O.render_fwd(rec, ranges, vals, V, W, H, tile, sc.cams, (0.0, 0.0, 0.0), tgt_rgb, tgt_d, 0.1, tol=1e-5)
+    ref = O.render_bwd(rec, ranges, vals, V, n, W, H, tile, sc.cams, fw["img"], fw["depth"], tgt_rgb, tgt_d,
+                       fw["depth_count"])
+    cfg = N.make_config(W, H, tile, bd, sc.sh_degree, 0.2, (0.0, 0.0, 0.0), 0.1)
+    g = rec_to_gpu(rec, pre["radius"], pre["clamp"])
+    cap = len(vals) + 16
+    gv, gr, go, ninst, st = gpu_bin(N, g, n, V, cfg, cap)
+    assert st == 0
+    Ttot = N.cgs_tiles_per_view(cfg) * V
+    nb = int(sum((int(e) - int(s0) + 31) // 32 for s0, e in ranges))
+    ckpt = torch.zeros(N.cgs_ckpt_bytes(nb, cfg) // 4, device="cuda")
+    bstart = torch.zeros(Ttot + 1, dtype=torch.int32, device="cuda")
+    out = {k: torch.zeros(V, 3, H, W, device="cuda") if k == "img" else torch.zeros(V, H, W, device="cuda")
+           for k in ("img", "depth", "T")}
+    last = torch.zeros(V, H, W, dtype=torch.int32, device="cuda")
+    loss = torch.zeros(V, device="cuda")
+    dcount = torch.zeros(V, dtype=torch.int32, device="cuda")
+    ws = torch.empty(N.cgs_render_fwd_workspace(V, cfg), dtype=torch.uint8, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    tr, td = torch.from_numpy(tgt_rgb).cuda(), torch.from_numpy(tgt_d).cuda()
+    w = torch.from_numpy(np.ascontiguousarray(sc.cams[:, 16])).cuda()
+    N.cgs_render_fwd_ckpt(g, gv, gr, go, V, cfg, w, tr, td, out["img"], out["depth"], out["T"], last, loss, dcount,
+                          ws, ckpt, nb, bstart, status)
+    sg = torch.zeros(V * n * 12, device="cuda")
+    N.cgs_raster_bwd_splat(g, gv, gr, go, V, cfg, w, out["img"], out["depth"], out["T"], last, tr, td, dcount,
+                           None, None, ckpt, nb, bstart, sg, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert int(bstart[-1].item()) == nb
+    ok = fw["near"] == 0
+    assert np.abs(out["img"].cpu().numpy() - fw["img"]).max(1)[ok].max() < PIX_TOL
+    gg = sg_from_gpu(sg)
+    fields = ["u", "v", "A", "B", "C", "o", "r", "g", "b", "z"]
+    errs = {f: rel_l2(gg[:, k], ref[:, k]) for k, f in enumerate(fields)}
+    print(f"[splat bwd {name}] " + " ".join(f"{f}:{e:.1e}" for f, e in errs.items()))
+    for f, e in errs.items():
+        assert e < GRAD_REL_TOL, (f, e)
+
+
+def test_splat_window_iteration_equals_pixel_window_iteration():
+    torch = torch_cuda()
+    native()
+    from paper_2410_00486_gb300.window import MappingWindow
+    sc, tgt_rgb, tgt_d = scene("path_sh3_3views")
+    params, cams = gpu_scene_tensors(sc)
+    wins = {}
+    for kind in ("pixel", "splat"):
+        win = MappingWindow(params.clone(), sc.n, 3, sc.width, sc.height, sc.views, tile=16, batch_depth=64,
+                            backward=kind)
+        win.set_window(cams, torch.from_numpy(tgt_rgb), torch.from_numpy(tgt_d))
+        win.fit_capacity()
+        win.forward()
+        win.backward()
+        torch.cuda.synchronize()
+        assert win.read_status()[0] == 0
+        wins[kind] = win
+    a, b = wins["pixel"], wins["splat"]
+    assert torch.equal(a.img, b.img) and torch.equal(a.last, b.last)
+    for k, sl in group_slices(sc.n, 3).items():
+        assert rel_l2(b.grads[sl].cpu().numpy(), a.grads[sl].cpu().numpy()) < 1e-4, k
+    assert torch.equal(a.denom, b.denom)
