@@ -286,3 +286,94 @@ class Scheduler:
 
     def report(self, index: int, loss: float):
         self.L[index] = float(loss)
+
+
+# ------------------------------------------------------------ densification
+
+SPLIT_CHILDREN = 2
+SPLIT_SCALE_DIV = 1.6          # children's scale = parent's / (0.8 * 2), as in 3DGS
+
+
+def densify_thresholds(tau_p, scale_thr, eps_alpha):
+    """Float32 decision thresholds, computed in double and rounded once: the gradient
+    threshold, log(scale threshold) and logit(eps_alpha)."""
+    return (np.float32(tau_p), np.float32(np.log(scale_thr)), np.float32(np.log(eps_alpha / (1.0 - eps_alpha))))
+
+
+def densify_plan(params, n, deg, accum, denom, tau_p, scale_thr, eps_alpha):
+    """Adaptive density control of 3DGS with the paper's thresholds (Sec. III-A.3, IV-A:
+    densify with positional-gradient threshold tau_p, remove Gaussians with opacity below
+    eps_alpha).  Decisions are taken in float32 (the kernel's precision):
+      grad = accum / denom (0 where denom = 0); high = grad >= tau_p;
+      small = max_i log s_i <= log(scale_thr);  prune = opacity logit < logit(eps_alpha)
+      clone = high & small & ~prune;  split = high & ~small & ~prune;  keep = ~prune & ~split
+    Returns (code, count) with code 0 prune, 1 keep, 2 keep + clone, 3 split; count =
+    outputs per Gaussian (0, 1, 2, 2)."""
+    t_grad, t_logs, t_logit = densify_thresholds(tau_p, scale_thr, eps_alpha)
+    P = np.asarray(params, np.float32)
+    acc = np.asarray(accum, np.float32)
+    den = np.asarray(denom, np.float32)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        grad = np.where(den > 0, acc / np.where(den > 0, den, np.float32(1)), np.float32(0)).astype(np.float32)
+    high = grad >= t_grad
+    logs = P[3 * n: 6 * n].reshape(n, 3)
+    small = logs.max(axis=1) <= t_logs
+    prune = P[10 * n: 11 * n] < t_logit
+    split = high & ~small & ~prune
+    clone = high & small & ~prune
+    code = np.where(prune, 0, np.where(split, 3, np.where(clone, 2, 1))).astype(np.int32)
+    count = np.array([0, 1, 2, 2], np.int64)[code]
+    return code, count
+
+
+def densify_apply(params, m, v, n, deg, code, normals):
+    """New parameter vector and Adam state after clone / split / prune, Gaussian by
+    Gaussian in order (reading: each Gaussian's outputs are consecutive):
+      keep  -> the Gaussian (with its Adam state)
+      clone -> the Gaussian (with its state), then a copy (zero state)
+      split -> two children: mean + R(q) (s * z_c) with z_c = normals[g, c] ~ N(0, I),
+               scale s / 1.6, other attributes copied, zero state
+      prune -> nothing.
+    Returns (params_out, m_out, v_out, n_out) in the flat layout for n_out Gaussians."""
+    K = (deg + 1) ** 2
+    widths = [3, 3, 4, 1, 3, 3 * (K - 1)]
+    offs = np.cumsum([0] + [w * n for w in widths])
+
+    def groups(a, nn):
+        o = np.cumsum([0] + [w * nn for w in widths])
+        return [np.asarray(a[o[i]:o[i + 1]]).reshape(nn, widths[i]) for i in range(6)]
+
+    Pg, Mg, Vg = groups(np.asarray(params, np.float64), n), groups(np.asarray(m, np.float64), n), \
+        groups(np.asarray(v, np.float64), n)
+    outP = [[] for _ in range(6)]
+    outM = [[] for _ in range(6)]
+    outV = [[] for _ in range(6)]
+    zero = [np.zeros(w) for w in widths]
+    for g in range(n):
+        c = code[g]
+        rows = []
+        if c in (1, 2):
+            rows.append(([Pg[i][g] for i in range(6)], [Mg[i][g] for i in range(6)], [Vg[i][g] for i in range(6)]))
+        if c == 2:
+            rows.append(([Pg[i][g] for i in range(6)], zero, zero))
+        if c == 3:
+            q = Pg[2][g] / np.linalg.norm(Pg[2][g])
+            w_, x, y, z = q
+            R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w_ * z), 2 * (x * z + w_ * y)],
+                          [2 * (x * y + w_ * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w_ * x)],
+                          [2 * (x * z - w_ * y), 2 * (y * z + w_ * x), 1 - 2 * (x * x + y * y)]])
+            s = np.exp(Pg[1][g])
+            for ci in range(SPLIT_CHILDREN):
+                mean = Pg[0][g] + R @ (s * np.asarray(normals[g, ci], np.float64))
+                logs = Pg[1][g] - np.log(SPLIT_SCALE_DIV)
+                rows.append(([mean, logs] + [Pg[i][g] for i in range(2, 6)], zero, zero))
+        for rp, rm, rv in rows:
+            for i in range(6):
+                outP[i].append(rp[i])
+                outM[i].append(rm[i])
+                outV[i].append(rv[i])
+    n_out = len(outP[0])
+    flat = lambda parts: np.concatenate([np.asarray(parts[i]).reshape(-1) for i in range(6)]) if n_out else \
+        np.zeros(0)
+    del offs
+    return flat(outP), flat(outM), flat(outV), n_out
