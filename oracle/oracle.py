@@ -377,3 +377,63 @@ def densify_apply(params, m, v, n, deg, code, normals):
         np.zeros(0)
     del offs
     return flat(outP), flat(outM), flat(outV), n_out
+
+
+# ----------------------------------------------------------------- SSIM term
+
+SSIM_C1 = 0.01 ** 2
+SSIM_C2 = 0.03 ** 2
+SSIM_WIN = 11
+SSIM_SIGMA = 1.5
+
+
+def ssim_window():
+    """Normalised 11-tap Gaussian (sigma 1.5); the 2-D window is its outer product."""
+    x = np.arange(SSIM_WIN) - SSIM_WIN // 2
+    g = np.exp(-(x * x) / (2.0 * SSIM_SIGMA ** 2))
+    return g / g.sum()
+
+
+def _blur(img):
+    """Zero-padded 'same' correlation of each [H, W] plane with the 2-D window."""
+    g = ssim_window()
+    r = SSIM_WIN // 2
+    H, W = img.shape[-2:]
+    pad = np.zeros(img.shape[:-2] + (H + 2 * r, W + 2 * r))
+    pad[..., r:r + H, r:r + W] = img
+    tmp = np.zeros(img.shape[:-2] + (H + 2 * r, W))
+    for k in range(SSIM_WIN):
+        tmp += g[k] * pad[..., :, k:k + W]
+    out = np.zeros(img.shape)
+    for k in range(SSIM_WIN):
+        out += g[k] * tmp[..., k:k + H, :]
+    return out
+
+
+def ssim_loss(img, tgt):
+    """Structural-similarity term of Eq. 9 per view: L_ssim = 1 - mean over channels and pixels
+    of SSIM, with mu, sigma^2, sigma_xy from the 11x11 Gaussian window (sigma 1.5, zero
+    padding), C1 = 0.01^2, C2 = 0.03^2 (reading: the 3DGS loss the paper keeps).
+    img, tgt: [V, 3, H, W].  Returns (loss[V], dloss/dimg [V, 3, H, W])."""
+    x = np.asarray(img, np.float64)
+    y = np.asarray(tgt, np.float64)
+    mx, my = _blur(x), _blur(y)
+    exx, eyy, exy = _blur(x * x), _blur(y * y), _blur(x * y)
+    sx, sy, sxy = exx - mx * mx, eyy - my * my, exy - mx * my
+    A1, A2 = 2 * mx * my + SSIM_C1, 2 * sxy + SSIM_C2
+    B1, B2 = mx * mx + my * my + SSIM_C1, sx + sy + SSIM_C2
+    S = (A1 * A2) / (B1 * B2)
+    M = x.shape[1] * x.shape[2] * x.shape[3]
+    loss = 1.0 - S.reshape(S.shape[0], -1).mean(axis=1)
+    # dS/d(mx), dS/d(E[x^2]), dS/d(E[xy]) per pixel (E = window mean), then back through the
+    # window: dL/dx = -(1/M) [ blur(a) + 2 x blur(b) + y blur(c) ]
+    dS_dA1 = A2 / (B1 * B2)
+    dS_dA2 = A1 / (B1 * B2)
+    dS_dB1 = -S / B1
+    dS_dB2 = -S / B2
+    # A1 = 2 mx my + C1, A2 = 2 (exy - mx my) + C2, B1 = mx^2 + my^2 + C1, B2 = exx - mx^2 + eyy - my^2 + C2
+    a = dS_dA1 * 2 * my + dS_dA2 * (-2 * my) + dS_dB1 * 2 * mx + dS_dB2 * (-2 * mx)
+    b = dS_dB2
+    c = dS_dA2 * 2
+    grad = -(_blur(a) + 2 * x * _blur(b) + y * _blur(c)) / M
+    return loss, grad
