@@ -302,6 +302,33 @@ int cgs_adam(float *params, const float *grads, float *m, float *v, int64_t n,
              int32_t step, int32_t *step_dev, float lambda_o, float *loss_o, void *stream);
 
 /*
+ * Adaptive density control (Sec. III-A.3: cloning and splitting "guided by gradients and
+ * the size", pruning transparent Gaussians; Sec. IV-A: tau_p = 0.001, eps_alpha = 0.02,
+ * every 500 iterations).  Two calls, so the caller can size the new buffers:
+ *   cgs_densify_plan: per Gaussian, in float32, grad = accum / denom (0 where denom = 0),
+ *     prune if opacity logit < logit(eps_alpha); otherwise split if grad >= tau_p and the
+ *     largest log-scale > log(scale_thr), clone if grad >= tau_p and it is <= log(scale_thr),
+ *     else keep.  Thresholds are rounded to float once from the double arguments.  Writes
+ *     the plan to the workspace (cgs_densify_workspace(n) bytes, 256-byte aligned) and the
+ *     new Gaussian count to *n_out_dev (device int64).
+ *   cgs_densify_apply: writes the new parameter vector and Adam moments for n_out
+ *     Gaussians, each input Gaussian's outputs consecutive: keep -> itself (its moments);
+ *     clone -> itself then a copy (zero moments); split -> two children at
+ *     mean + R(q) (s * z_c) with scale s / 1.6, other attributes copied, zero moments;
+ *     prune -> nothing.  normals: device float[n][2][3] standard normal samples z_c
+ *     (random numbers are inputs).  Outputs must not alias inputs.  The densification
+ *     statistics are the caller's to reset (zero) for the new Gaussians.
+ */
+size_t cgs_densify_workspace(int64_t n);
+int cgs_densify_plan(const float *params, int64_t n, int32_t sh_degree, const float *accum,
+                     const float *denom, double tau_p, double scale_thr, double eps_alpha,
+                     void *workspace, size_t workspace_bytes, int64_t *n_out_dev, void *stream);
+int cgs_densify_apply(const float *params, const float *m, const float *v, int64_t n,
+                      int32_t sh_degree, const void *workspace, size_t workspace_bytes,
+                      const float *normals, int64_t n_out, float *params_out, float *m_out,
+                      float *v_out, void *stream);
+
+/*
  * Adaptive keyframe scheduler (Eqs. 5-8, Sec. III-C.2), host only.  A pool of
  * keyframes with remaining iteration counts r_i and last losses l_i; a draw picks
  * uniformly (index = rand_u32 mod count, in pool order) among keyframes with

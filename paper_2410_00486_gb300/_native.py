@@ -74,6 +74,10 @@ _SIGS = {
     "cgs_densify_stats": (c_int32, [_P, _P, c_int64, c_int32, _P, _P, _P, _P, _P]),
     "cgs_adam": (c_int32, [_P, _P, _P, _P, c_int64, c_int32, _P, c_float, c_float, c_float, c_int32,
                            _P, c_float, _P, _P]),
+    "cgs_densify_workspace": (c_size_t, [c_int64]),
+    "cgs_densify_plan": (c_int32, [_P, c_int64, c_int32, _P, _P, c_double, c_double, c_double, _P, c_size_t, _P,
+                                   _P]),
+    "cgs_densify_apply": (c_int32, [_P, _P, _P, c_int64, c_int32, _P, c_size_t, _P, c_int64, _P, _P, _P, _P]),
     "cgs_sched_create": (_P, [c_int32]),
     "cgs_sched_destroy": (None, [_P]),
     "cgs_sched_add": (c_int32, [_P, c_int32, c_int32]),
@@ -248,6 +252,27 @@ def cgs_adam(params, grads, m, v, n, sh_degree, lr, beta1, beta2, eps, step, lam
     _check("cgs_adam", lib().cgs_adam(_dev(params), _dev(grads), _dev(m), _dev(v), n, sh_degree,
                                       ctypes.cast(lr6, c_void_p), beta1, beta2, eps, step, _dev(step_dev),
                                       lambda_o, _dev(loss_o), _stream(stream)))
+
+
+def cgs_densify_workspace(n) -> int:
+    return lib().cgs_densify_workspace(n)
+
+
+def cgs_densify_plan(params, n, sh_degree, accum, denom, tau_p, scale_thr, eps_alpha, workspace, n_out,
+                     stream=None):
+    nbytes = workspace.numel() * workspace.element_size()
+    _check("cgs_densify_plan", lib().cgs_densify_plan(_dev(params), n, sh_degree, _dev(accum), _dev(denom),
+                                                      float(tau_p), float(scale_thr), float(eps_alpha),
+                                                      _dev(workspace), nbytes, _dev(n_out), _stream(stream)))
+
+
+def cgs_densify_apply(params, m, v, n, sh_degree, workspace, normals, n_out, params_out, m_out, v_out,
+                      stream=None):
+    nbytes = workspace.numel() * workspace.element_size()
+    _check("cgs_densify_apply", lib().cgs_densify_apply(_dev(params), _dev(m), _dev(v), n, sh_degree,
+                                                        _dev(workspace), nbytes, _dev(normals), n_out,
+                                                        _dev(params_out), _dev(m_out), _dev(v_out),
+                                                        _stream(stream)))
 
 
 class Scheduler:

@@ -55,7 +55,7 @@ class MappingWindow:
         self.lambda_o = float(lambda_o)
         self.betas = (float(betas[0]), float(betas[1]))
         self.eps = float(eps)
-        self.densify = densify_stats
+        self.track_stats = densify_stats
         if backward not in ("pixel", "splat"):
             raise ValueError("backward must be 'pixel' or 'splat'")
         self.backward_kind = backward
@@ -152,7 +152,7 @@ class MappingWindow:
                  grads_out: torch.Tensor | None = None):
         """Raster backward + chain rule to the parameters; overwrites self.grads (or
         grads_out).  Pixel gradients come from the fused L1 loss unless dl_dimg is given."""
-        d = self.densify and dl_dimg is None
+        d = self.track_stats
         p = self.params if params is None else params
         g = self.grads if grads_out is None else grads_out
         if self.backward_kind == "splat":
@@ -180,6 +180,52 @@ class MappingWindow:
         self.backward()
         self.optimizer_step()
 
+    # ------------------------------------------------------ densification
+    def densify(self, tau_p: float = 0.001, eps_alpha: float = 0.02, percent_dense: float = 0.01,
+                extent: float = 1.0, normals: torch.Tensor | None = None, seed: int = 0) -> dict:
+        """Adaptive density control with the paper's thresholds (Sec. III-A.3, IV-A): clone
+        small high-gradient Gaussians, split large ones in two, prune those with opacity below
+        eps_alpha.  The gradient statistics are the accumulated view-space norms / counts of
+        the iterations since the last call; they restart at zero.  Changes the number of
+        Gaussians, so every per-Gaussian buffer is reallocated and a captured graph dropped.
+        `normals` (float32 [n, 2, 3], standard normal) are the split samples; drawn from a
+        seeded generator if not given."""
+        n, deg = self.n, self.sh_degree
+        ws = torch.empty(max(256, N.cgs_densify_workspace(n)), dtype=torch.uint8, device=self.device)
+        n_out_dev = torch.zeros(1, dtype=torch.int64, device=self.device)
+        N.cgs_densify_plan(self.params, n, deg, self.accum, self.denom, tau_p, percent_dense * extent, eps_alpha,
+                           ws, n_out_dev)
+        n_out = int(n_out_dev.item())
+        if normals is None:
+            gen = torch.Generator(device=self.device)
+            gen.manual_seed(seed)
+            normals = torch.randn(n, 2, 3, generator=gen, device=self.device)
+        P2 = N.cgs_param_count(max(n_out, 1), deg)
+        f32 = dict(dtype=torch.float32, device=self.device)
+        p2, m2, v2 = torch.zeros(P2, **f32), torch.zeros(P2, **f32), torch.zeros(P2, **f32)
+        N.cgs_densify_apply(self.params, self.m, self.v, n, deg, ws, normals.contiguous(), n_out, p2, m2, v2)
+        code = ws[: 4 * n].view(torch.int32)
+        counts = torch.bincount(code.long(), minlength=4).cpu().tolist()
+        if n_out == 0:
+            raise RuntimeError("densification pruned every Gaussian")
+        self._resize(n_out, p2, m2, v2)
+        return {"pruned": counts[0], "kept": counts[1], "cloned": counts[2], "split": counts[3], "n": n_out}
+
+    def _resize(self, n: int, params: torch.Tensor, m: torch.Tensor, v: torch.Tensor):
+        f32 = dict(dtype=torch.float32, device=self.device)
+        self.n = int(n)
+        self.P = N.cgs_param_count(self.n, self.sh_degree)
+        self.params, self.m, self.v = params, m, v
+        self.grads = torch.zeros(self.P, **f32)
+        slots = self.V * self.n
+        self.rec = torch.zeros(slots * N.REC_FLOATS, **f32)
+        self.slot_grad = torch.zeros(slots * N.REC_FLOATS, **f32)
+        self.accum = torch.zeros(self.n, **f32)
+        self.denom = torch.zeros(self.n, **f32)
+        self.max_r2d = torch.zeros(self.n, **f32)
+        self._pv = None
+        self.graph = None
+
     # ------------------------------------------------------- per-view form
     def _per_view_buffers(self):
         if self._pv is None:
@@ -200,7 +246,7 @@ class MappingWindow:
         """The same iteration, one view at a time (gradients accumulated, one Adam step)."""
         pv = self._per_view_buffers()
         c = self.cfg
-        d = self.densify
+        d = self.track_stats
         for v in range(self.V):
             cam = self.cams[v:v + 1]
             N.cgs_preprocess(self.params, self.n, cam, 1, c, pv["rec"], pv["slot_grad"], self.status)

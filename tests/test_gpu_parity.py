@@ -601,3 +601,65 @@ def test_splat_window_iteration_equals_pixel_window_iteration():
     for k, sl in group_slices(sc.n, 3).items():
         assert rel_l2(b.grads[sl].cpu().numpy(), a.grads[sl].cpu().numpy()) < 1e-4, k
     assert torch.equal(a.denom, b.denom)
+
+
+# ------------------------------------------------------------ densification
+
+def test_densify_matches_oracle():
+    """Clone / split / prune decisions bit-exact with the oracle (both in float32), copied
+    Gaussians and moments exact, split children within float32 rounding."""
+    torch = torch_cuda()
+    N = native()
+    sc = make_scene(3, n=4000)
+    n, deg = sc.n, sc.sh_degree
+    rng = np.random.default_rng(9)
+    params = sc.params.copy()
+    params[3 * n: 6 * n] = rng.normal(-4.0, 1.2, 3 * n).astype(np.float32)     # a mix of small and big
+    params[10 * n: 11 * n] = rng.normal(0.0, 2.5, n).astype(np.float32)        # some below logit(0.02)
+    accum = rng.uniform(0.0, 0.004, n).astype(np.float32)
+    denom = rng.integers(0, 4, n).astype(np.float32)
+    m = rng.normal(size=params.size).astype(np.float32)
+    v = rng.uniform(0, 1, params.size).astype(np.float32)
+    normals = rng.normal(size=(n, 2, 3)).astype(np.float32)
+    code_o, count_o = O.densify_plan(params, n, deg, accum, denom, 0.001, 0.01 * 3.0, 0.02)
+    assert {0, 1, 2, 3} <= set(code_o.tolist())
+    P_o, M_o, V_o, n_o = O.densify_apply(params, m, v, n, deg, code_o, normals)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()   # noqa: E731
+    ws = torch.empty(N.cgs_densify_workspace(n), dtype=torch.uint8, device="cuda")
+    nout = torch.zeros(1, dtype=torch.int64, device="cuda")
+    N.cgs_densify_plan(t(params), n, deg, t(accum), t(denom), 0.001, 0.01 * 3.0, 0.02, ws, nout)
+    torch.cuda.synchronize()
+    assert int(nout.item()) == n_o
+    assert np.array_equal(ws[: 4 * n].view(torch.int32).cpu().numpy(), code_o)
+    P2 = N.cgs_param_count(n_o, deg)
+    p2, m2, v2 = (torch.zeros(P2, device="cuda") for _ in range(3))
+    N.cgs_densify_apply(t(params), t(m), t(v), n, deg, ws, t(normals), n_o, p2, m2, v2)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(m2.cpu().numpy(), M_o.astype(np.float32))
+    np.testing.assert_array_equal(v2.cpu().numpy(), V_o.astype(np.float32))
+    got = p2.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got, P_o, rtol=2e-6, atol=2e-7)
+
+
+def test_window_densify_then_iterate():
+    torch = torch_cuda()
+    native()
+    from paper_2410_00486_gb300.window import MappingWindow
+    sc, tgt_rgb, tgt_d = scene("cfg3")
+    params, cams = gpu_scene_tensors(sc)
+    win = MappingWindow(params.clone(), sc.n, sc.sh_degree, sc.width, sc.height, 1, tile=16)
+    win.set_window(cams, torch.from_numpy(tgt_rgb), torch.from_numpy(tgt_d))
+    win.fit_capacity(2.0)
+    for _ in range(3):
+        win.step()
+    torch.cuda.synchronize()
+    assert win.denom.max().item() == 3.0
+    stats = win.densify(tau_p=1e-4, eps_alpha=0.02, percent_dense=0.01, extent=3.0)
+    assert stats["n"] == stats["kept"] + 2 * stats["cloned"] + 2 * stats["split"]
+    assert stats["cloned"] + stats["split"] > 0 and win.n == stats["n"]
+    assert win.denom.abs().sum().item() == 0.0
+    win.fit_capacity(2.0)
+    win.step()
+    torch.cuda.synchronize()
+    assert win.read_status()[0] == 0
+    assert torch.isfinite(win.params).all()
