@@ -542,7 +542,9 @@ static double sgn(double x) { return x > 0 ? 1.0 : (x < 0 ? -1.0 : 0.0); }
 
 /*
  * Backward of the blend (Eqs. 2-4): for every pixel, dL/dimg and dL/ddepth from the
- * L1 loss (d|r|/dr = sign(r), 0 at r = 0, reading); then, for every blended splat k
+ * L1 loss (d|r|/dr = sign(r), 0 at r = 0, reading), or the caller's pixel gradients
+ * gimg [V][3][H][W] and gdepth [V][H][W] (NULL: zero) when gimg is non-NULL (the loss
+ * of Eq. 9 with its SSIM term); then, for every blended splat k
  * of that pixel (T_k kept from the forward walk, no division):
  *   dI/dc_k = alpha_k T_k,  dD/dz_k = alpha_k T_k
  *   dI/dalpha_k = c_k T_k - (S_k + T_final bg) / (1 - alpha_k),
@@ -557,7 +559,7 @@ int orc_render_bwd(const double *rec, const uint32_t *ranges, const uint32_t *va
                    int64_t n, int W, int H, int B, const double *bg, const double *cams,
                    const double *img, const double *depth, const double *tgt_rgb,
                    const double *tgt_depth, const int64_t *depth_count, double lambda_d,
-                   double *grads)
+                   const double *gimg, const double *gdepth, double *grads)
 {
     int Tx = (W + B - 1) / B, Ty = (H + B - 1) / B;
     int64_t HW = (int64_t)H * W;
@@ -584,9 +586,11 @@ int orc_render_bwd(const double *rec, const uint32_t *ranges, const uint32_t *va
                 double gI[3], gD = 0.0;
                 for (int ch = 0; ch < 3; ch++) {
                     int64_t q = ((int64_t)v * 3 + ch) * HW + (int64_t)y * W + x;
-                    gI[ch] = w * sgn(img[q] - tgt_rgb[q]) / (3.0 * HW);
+                    gI[ch] = gimg ? gimg[q] : w * sgn(img[q] - tgt_rgb[q]) / (3.0 * HW);
                 }
-                if (tgt_depth && tgt_depth[p] > 0.0 && depth_count[v] > 0)
+                if (gimg)
+                    gD = gdepth ? gdepth[p] : 0.0;
+                else if (tgt_depth && tgt_depth[p] > 0.0 && depth_count[v] > 0)
                     gD = w * lambda_d * sgn(depth[p] - tgt_depth[p]) / (double)depth_count[v];
                 /* suffix sums S_k of contributions behind k */
                 for (int j = 0; j < 4; j++) S[4 * nb + j] = 0.0;

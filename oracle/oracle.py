@@ -60,7 +60,7 @@ def _load():
         lib.orc_render_fwd.argtypes = [P, P, P, i32, i32, i32, i32, P, P, P, P, f64, f64,
                                        P, P, P, P, P, P, P, P]
         lib.orc_render_bwd.argtypes = [P, P, P, i32, i64, i32, i32, i32, P, P, P, P, P, P, P,
-                                       f64, P]
+                                       f64, P, P, P]
         lib.orc_preprocess_bwd.argtypes = [P, i64, i32, P, i32, i32, i32, i32, f64, P, P]
         lib.orc_densify_stats.argtypes = [P, P, i32, i64, i32, i32, P, P, P]
         lib.orc_sh_basis.argtypes = [i32, f64, f64, f64, P, P]
@@ -165,15 +165,20 @@ def render_pixels(rec, ranges, vals, W, H, B, pix, bg=(0.0, 0.0, 0.0), tol=0.0) 
 
 
 def render_bwd(rec, ranges, vals, V, n, W, H, B, cams, img, depth, tgt_rgb, tgt_depth,
-               depth_count, bg=(0.0, 0.0, 0.0), lambda_d=0.1) -> np.ndarray:
+               depth_count, bg=(0.0, 0.0, 0.0), lambda_d=0.1, dl_dimg=None, dl_ddepth=None) -> np.ndarray:
+    """Slot gradients [V*n][10]; pixel gradients from the fused L1 loss, or dl_dimg
+    [V,3,H,W] / dl_ddepth [V,H,W] (None: zero) when dl_dimg is given."""
     lib = _load()
     grads = np.zeros((V * n, NREC))
     td = _f64(tgt_depth) if tgt_depth is not None else None
+    gi = _f64(dl_dimg) if dl_dimg is not None else None
+    gd = _f64(dl_ddepth) if dl_ddepth is not None else None
     lib.orc_render_bwd(_p(_f64(rec)), _p(np.ascontiguousarray(ranges, np.uint32)),
                        _p(np.ascontiguousarray(vals, np.uint32)), V, n, W, H, B, _p(_f64(bg)),
                        _p(cams_to_oracle(cams)), _p(_f64(img)), _p(_f64(depth)), _p(_f64(tgt_rgb)),
                        _p(td) if td is not None else None,
-                       _p(np.ascontiguousarray(depth_count, np.int64)), lambda_d, _p(grads))
+                       _p(np.ascontiguousarray(depth_count, np.int64)), lambda_d,
+                       _p(gi) if gi is not None else None, _p(gd) if gd is not None else None, _p(grads))
     return grads
 
 
@@ -225,20 +230,26 @@ def lr_per_element(n, deg, lr6):
 
 
 def iteration(params, n, deg, cams, W, H, B, tgt_rgb, tgt_depth, bg=(0.0, 0.0, 0.0),
-              lambda_d=0.1, lambda_o=0.0, near=0.2, tol=0.0) -> dict:
-    """Loss and parameter gradient of one window iteration, plus every intermediate."""
+              lambda_d=0.1, lambda_o=0.0, near=0.2, tol=0.0, lambda_ssim=0.0) -> dict:
+    """Loss and parameter gradient of one window iteration, plus every intermediate.
+    lambda_ssim > 0 adds the SSIM term of Eq. 9 (photometric_loss); 0 keeps the L1 form."""
     V = np.asarray(cams).shape[0]
     pre = preprocess(params, n, deg, cams, W, H, B, near)
     rec = pre["rec"]
     ranges, vals = bin_lists(rec[:, 0], rec[:, 1], rec[:, 9], pre["radius"], V, n, W, H, B)
     fw = render_fwd(rec, ranges, vals, V, W, H, B, cams, bg, tgt_rgb, tgt_depth, lambda_d, tol)
+    loss_view = fw["loss_view"]
+    gi = gd = None
+    if lambda_ssim > 0.0:
+        loss_view, gi, gd = photometric_loss(fw["img"], fw["depth"], tgt_rgb, tgt_depth,
+                                             np.asarray(cams)[:, 16], lambda_ssim, lambda_d)
     sg = render_bwd(rec, ranges, vals, V, n, W, H, B, cams, fw["img"], fw["depth"], tgt_rgb,
-                    tgt_depth, fw["depth_count"], bg, lambda_d)
+                    tgt_depth, fw["depth_count"], bg, lambda_d, gi, gd)
     grads = preprocess_bwd(params, n, deg, cams, W, H, B, sg, near)
     lo, glo = opacity_reg(params, n, lambda_o)
     grads[10 * n: 11 * n] += glo
     return dict(pre=pre, ranges=ranges, vals=vals, fwd=fw, slot_grads=sg, grads=grads,
-                loss=float(fw["loss_view"].sum() + lo), loss_o=lo)
+                loss_view=loss_view, loss=float(loss_view.sum() + lo), loss_o=lo)
 
 
 # ------------------------------------------------------ adaptive scheduler
@@ -437,3 +448,31 @@ def ssim_loss(img, tgt):
     c = dS_dA2 * 2
     grad = -(_blur(a) + 2 * x * _blur(b) + y * _blur(c)) / M
     return loss, grad
+
+
+def photometric_loss(img, depth, tgt_rgb, tgt_depth, weight, lambda_ssim, lambda_d=0.1):
+    """Per-view loss of Eq. 9 with the depth term: L_v = w_v [ (1 - l) L1 + l L_ssim +
+    lambda_d mean over {tgt_depth > 0} of |D - D*| ], l = lambda_ssim, L1 the mean over
+    channels and pixels of |img - tgt| (sign(0) = 0).  tgt_depth may be None (no depth
+    term).  Returns (loss[V], dL/dimg [V,3,H,W], dL/ddepth [V,H,W])."""
+    x = np.asarray(img, np.float64)
+    y = np.asarray(tgt_rgb, np.float64)
+    V = x.shape[0]
+    w = np.asarray(weight, np.float64).reshape(V)
+    M = x.shape[1] * x.shape[2] * x.shape[3]
+    l1 = np.abs(x - y).reshape(V, -1).mean(axis=1)
+    ls, gs = ssim_loss(x, y)
+    loss = (1.0 - lambda_ssim) * l1 + lambda_ssim * ls
+    g_img = (1.0 - lambda_ssim) * np.sign(x - y) / M + lambda_ssim * gs
+    g_dep = np.zeros(x.shape[:1] + x.shape[2:])
+    if tgt_depth is not None:
+        D = np.asarray(depth, np.float64)
+        Dt = np.asarray(tgt_depth, np.float64)
+        mask = Dt > 0.0
+        cnt = mask.reshape(V, -1).sum(axis=1)
+        r = np.where(mask, D - Dt, 0.0)
+        for v in range(V):
+            if cnt[v] > 0:
+                loss[v] += lambda_d * np.abs(r[v]).sum() / cnt[v]
+                g_dep[v] = lambda_d * np.sign(r[v]) / cnt[v]
+    return w * loss, w[:, None, None, None] * g_img, w[:, None, None] * g_dep
