@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stages", action="store_true")
     ap.add_argument("--no-splat", action="store_true", help="skip the splat-wise backward head-to-head")
+    ap.add_argument("--no-ssim", action="store_true", help="skip the timing of the loss with its SSIM term")
+    ap.add_argument("--lambda-ssim", type=float, default=0.2)
     return ap.parse_args()
 
 
@@ -337,6 +339,12 @@ def main():
         splat = splat_head_to_head(MappingWindow, params_t, sc, tile, bd, cams, tgt_rgb, tgt_d, win.capacity,
                                    max(3, args.steps // 4), args.warmup, value / world)
 
+    # --- the same iteration with the SSIM term of Eq. 9 in the loss
+    ssim = None
+    if not args.no_ssim:
+        ssim = ssim_variant(MappingWindow, params_t, sc, tile, bd, cams, tgt_rgb, tgt_d, win.capacity,
+                            max(3, args.steps // 4), args.warmup, args.lambda_ssim)
+
     # --- stage breakdown (eager, CUDA events on the launching stream)
     stages = None
     work = None
@@ -370,6 +378,7 @@ def main():
             "view_iters_per_s": value * V,
             "per_view_form": per_view,
             "splat_backward": splat,
+            "ssim_loss_form": ssim,
             "e2e": {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
             if e2e else None,
             "gpu_launches": gpu_launches,
@@ -424,6 +433,42 @@ def splat_head_to_head(MappingWindow, params_t, sc, tile, bd, cams, tgt_rgb, tgt
            "raster_bwd_splat_ms": round(ev[1].elapsed_time(ev[2]), 4),
            "checkpoint_buckets": int(w.bucket_start[-1].item()),
            "pixel_wise_over_splat_wise": pixel_value / (1e3 / ms)}
+    del w
+    torch.cuda.empty_cache()
+    return out
+
+
+def ssim_variant(MappingWindow, params_t, sc, tile, bd, cams, tgt_rgb, tgt_d, capacity, k, warmup, lam):
+    """Window iterations/s with the loss of Eq. 9 including its SSIM term (weight lam), and the
+    time of the SSIM loss stage alone."""
+    import torch
+    from paper_2410_00486_gb300 import _native as N
+    w = MappingWindow(params_t.clone(), sc.n, sc.sh_degree, sc.width, sc.height, sc.views, tile=tile,
+                      batch_depth=bd, capacity=capacity, lambda_ssim=lam)
+    w.set_window(cams, tgt_rgb, tgt_d)
+    w.capture()
+    for _ in range(warmup):
+        w.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(k):
+        w.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    st = w.read_status()
+    if st[0] != 0:
+        raise SystemExit(f"device status (SSIM loss): {st}")
+    reps = 5
+    e0.record()
+    for _ in range(reps):
+        N.cgs_ssim_loss(w.img, w.tgt_rgb, w.depth, w.tgt_depth, w.depth_count, w.V, w.cfg, w.view_weight, lam,
+                        w.loss_view, w.dl_dimg, w.dl_ddepth, w.ssim_ws, w.status)
+    e1.record()
+    torch.cuda.synchronize()
+    out = {"lambda_ssim": lam, "value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "steps": k,
+           "ssim_loss_ms": round(e0.elapsed_time(e1) / reps, 4)}
     del w
     torch.cuda.empty_cache()
     return out

@@ -329,6 +329,30 @@ int cgs_densify_apply(const float *params, const float *m, const float *v, int64
                       float *v_out, void *stream);
 
 /*
+ * cgs_ssim_loss -- the photometric loss of Eq. 9 with its SSIM term (Sec. III-C.3), plus the
+ * depth term, and its pixel gradients for the blend backward (cgs_render_bwd /
+ * cgs_raster_bwd / cgs_raster_bwd_splat with dl_dimg, dl_ddepth non-NULL):
+ *   loss_view[v] = w_v [ (1 - l) mean|img - tgt| + l (1 - mean SSIM) + lambda_depth
+ *                   mean over {tgt_depth > 0} |depth - tgt_depth| ],  l = lambda_ssim in [0, 1]
+ * SSIM per pixel and channel from 11x11 Gaussian-window (sigma 1.5) moments with zero
+ * padding, C1 = 0.01^2, C2 = 0.03^2 (the 3D Gaussian Splatting loss the paper keeps).
+ * img, tgt_rgb: device float[V][3][H][W]; depth, tgt_depth: float[V][H][W] (tgt_depth
+ * NULL: no depth term; then depth, depth_count, dl_ddepth are not read or written);
+ * depth_count: int32[V] = |{tgt_depth > 0}| per view (cgs_render_fwd writes it);
+ * view_weight: float[V] or NULL (all 1).  Writes loss_view float[V] (overwritten),
+ * dl_dimg float[V][3][H][W] and dl_ddepth float[V][H][W] (all overwritten).  The
+ * workspace (cgs_ssim_workspace(V, cfg) bytes, 256-byte aligned) holds three per-pixel
+ * partial-derivative maps and the per-view sums.  Reads only cfg->width, height and
+ * lambda_depth.  A non-finite loss sets CGS_ERR_NONFINITE in *status_dev.
+ */
+size_t cgs_ssim_workspace(int32_t V, const cgs_config *cfg);
+int cgs_ssim_loss(const float *img, const float *tgt_rgb, const float *depth,
+                  const float *tgt_depth, const int32_t *depth_count, int32_t V,
+                  const cgs_config *cfg, const float *view_weight, float lambda_ssim,
+                  float *loss_view, float *dl_dimg, float *dl_ddepth, void *workspace,
+                  size_t workspace_bytes, int32_t *status_dev, void *stream);
+
+/*
  * Adaptive keyframe scheduler (Eqs. 5-8, Sec. III-C.2), host only.  A pool of
  * keyframes with remaining iteration counts r_i and last losses l_i; a draw picks
  * uniformly (index = rand_u32 mod count, in pool order) among keyframes with

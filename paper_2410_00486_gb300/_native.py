@@ -78,6 +78,9 @@ _SIGS = {
     "cgs_densify_plan": (c_int32, [_P, c_int64, c_int32, _P, _P, c_double, c_double, c_double, _P, c_size_t, _P,
                                    _P]),
     "cgs_densify_apply": (c_int32, [_P, _P, _P, c_int64, c_int32, _P, c_size_t, _P, c_int64, _P, _P, _P, _P]),
+    "cgs_ssim_workspace": (c_size_t, [c_int32, _P]),
+    "cgs_ssim_loss": (c_int32, [_P, _P, _P, _P, _P, c_int32, _P, _P, c_float, _P, _P, _P, _P, c_size_t, _P,
+                                _P]),
     "cgs_sched_create": (_P, [c_int32]),
     "cgs_sched_destroy": (None, [_P]),
     "cgs_sched_add": (c_int32, [_P, c_int32, c_int32]),
@@ -273,6 +276,20 @@ def cgs_densify_apply(params, m, v, n, sh_degree, workspace, normals, n_out, par
                                                         _dev(workspace), nbytes, _dev(normals), n_out,
                                                         _dev(params_out), _dev(m_out), _dev(v_out),
                                                         _stream(stream)))
+
+
+def cgs_ssim_workspace(V, cfg) -> int:
+    return lib().cgs_ssim_workspace(V, byref(cfg))
+
+
+def cgs_ssim_loss(img, tgt_rgb, depth, tgt_depth, depth_count, V, cfg, view_weight, lambda_ssim, loss_view,
+                  dl_dimg, dl_ddepth, workspace, status=None, stream=None):
+    nbytes = workspace.numel() * workspace.element_size()
+    _check("cgs_ssim_loss", lib().cgs_ssim_loss(_dev(img), _dev(tgt_rgb), _dev(depth), _dev(tgt_depth),
+                                                _dev(depth_count), V, byref(cfg), _dev(view_weight),
+                                                float(lambda_ssim), _dev(loss_view), _dev(dl_dimg),
+                                                _dev(dl_ddepth), _dev(workspace), nbytes, _dev(status),
+                                                _stream(stream)))
 
 
 class Scheduler:

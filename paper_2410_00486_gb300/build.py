@@ -20,7 +20,7 @@ BUILD = PKG / "_build"
 LIB = BUILD / "libcgs.so"
 
 CUDA_SOURCES = ["preprocess.cu", "binsort.cu", "render_fwd.cu", "render_bwd.cu", "render_bwd_splat.cu", "adam.cu",
-                "densify.cu", "capi.cu"]
+                "densify.cu", "ssim.cu", "capi.cu"]
 CPP_SOURCES = ["sched.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -39,7 +39,8 @@ class MappingWindow:
                  tile: int = 16, batch_depth: int = 64, lr=LR_DEFAULT, lambda_o: float = 0.0,
                  lambda_depth: float = 0.1, bg=(0.0, 0.0, 0.0), near_z: float = 0.2,
                  betas=(0.9, 0.999), eps: float = 1e-15, capacity: int | None = None,
-                 densify_stats: bool = True, tile_order: bool = True, backward: str = "pixel"):
+                 densify_stats: bool = True, tile_order: bool = True, backward: str = "pixel",
+                 lambda_ssim: float = 0.0):
         if not params.is_cuda or params.dtype != torch.float32:
             raise ValueError("params must be a float32 CUDA tensor")
         dev = params.device
@@ -59,6 +60,9 @@ class MappingWindow:
         if backward not in ("pixel", "splat"):
             raise ValueError("backward must be 'pixel' or 'splat'")
         self.backward_kind = backward
+        if not 0.0 <= lambda_ssim <= 1.0:
+            raise ValueError("lambda_ssim must lie in [0, 1]")
+        self.lambda_ssim = float(lambda_ssim)
         f32 = dict(dtype=torch.float32, device=dev)
 
         self.params = params.contiguous()
@@ -92,6 +96,11 @@ class MappingWindow:
         self.loss_o = torch.zeros(1, **f32)
         self.fwd_ws = torch.empty(max(256, N.cgs_render_fwd_workspace(V, self.cfg)), dtype=torch.uint8,
                                   device=dev)
+        if self.lambda_ssim > 0.0:
+            # Eq. 9 with its SSIM term: the loss kernel writes the pixel gradients
+            self.dl_dimg = torch.zeros(V, 3, H, W, **f32)
+            self.dl_ddepth = torch.zeros(V, H, W, **f32)
+            self.ssim_ws = torch.empty(N.cgs_ssim_workspace(V, self.cfg), dtype=torch.uint8, device=dev)
         self.accum = torch.zeros(self.n, **f32)
         self.denom = torch.zeros(self.n, **f32)
         self.max_r2d = torch.zeros(self.n, **f32)
@@ -129,7 +138,8 @@ class MappingWindow:
 
     # ---------------------------------------------------------- iteration
     def forward(self, with_loss: bool = True, params: torch.Tensor | None = None):
-        """Preprocess, bin and render every view of the window (loss fused if with_loss).
+        """Preprocess, bin and render every view of the window (loss fused if with_loss;
+        with lambda_ssim > 0 the loss of Eq. 9 and its pixel gradients follow the render).
         `params` overrides the window's own parameter vector (same layout)."""
         c = self.cfg
         p = self.params if params is None else params
@@ -147,12 +157,19 @@ class MappingWindow:
                              self.tgt_rgb if with_loss else None, self.tgt_depth if with_loss else None,
                              self.img, self.depth, self.t_final, self.last, self.loss_view, self.depth_count,
                              self.fwd_ws, self.status)
+        if with_loss and self.lambda_ssim > 0.0:
+            N.cgs_ssim_loss(self.img, self.tgt_rgb, self.depth, self.tgt_depth, self.depth_count, self.V, c,
+                            self.view_weight, self.lambda_ssim, self.loss_view, self.dl_dimg, self.dl_ddepth,
+                            self.ssim_ws, self.status)
 
     def backward(self, dl_dimg=None, dl_ddepth=None, params: torch.Tensor | None = None,
                  grads_out: torch.Tensor | None = None):
         """Raster backward + chain rule to the parameters; overwrites self.grads (or
-        grads_out).  Pixel gradients come from the fused L1 loss unless dl_dimg is given."""
+        grads_out).  Pixel gradients come from the fused L1 loss unless dl_dimg is given
+        (or the window has an SSIM term, whose gradients the forward wrote)."""
         d = self.track_stats
+        if dl_dimg is None and self.lambda_ssim > 0.0:
+            dl_dimg, dl_ddepth = self.dl_dimg, self.dl_ddepth
         p = self.params if params is None else params
         g = self.grads if grads_out is None else grads_out
         if self.backward_kind == "splat":
@@ -239,6 +256,8 @@ class MappingWindow:
                                    device=dev)
             pv["fwd_ws"] = torch.empty(max(256, N.cgs_render_fwd_workspace(1, self.cfg)), dtype=torch.uint8,
                                        device=dev)
+            if self.lambda_ssim > 0.0:
+                pv["ssim_ws"] = torch.empty(N.cgs_ssim_workspace(1, self.cfg), dtype=torch.uint8, device=dev)
             self._pv = pv
         return self._pv
 
@@ -257,8 +276,13 @@ class MappingWindow:
             w, lv, dc = self.view_weight[v:v + 1], self.loss_view[v:v + 1], self.depth_count[v:v + 1]
             N.cgs_render_fwd(pv["rec"], self.vals, pv["ranges"], pv["order"], 1, c, w, tr, td, img, dep, tf, la,
                              lv, dc, pv["fwd_ws"], self.status)
+            gi = gd = None
+            if self.lambda_ssim > 0.0:
+                gi, gd = self.dl_dimg[v:v + 1], self.dl_ddepth[v:v + 1]
+                N.cgs_ssim_loss(img, tr, dep, td, dc, 1, c, w, self.lambda_ssim, lv, gi, gd, pv["ssim_ws"],
+                                self.status)
             N.cgs_render_bwd(self.params, self.n, cam, 1, c, pv["rec"], self.vals, pv["ranges"], pv["order"], w,
-                             img, dep, tf, la, tr, td, dc, None, None, pv["slot_grad"], self.grads, v > 0,
+                             img, dep, tf, la, tr, td, dc, gi, gd, pv["slot_grad"], self.grads, v > 0,
                              self.accum if d else None, self.denom if d else None, self.max_r2d if d else None,
                              self.status)
         self.optimizer_step()

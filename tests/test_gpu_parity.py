@@ -663,3 +663,131 @@ def test_window_densify_then_iterate():
     torch.cuda.synchronize()
     assert win.read_status()[0] == 0
     assert torch.isfinite(win.params).all()
+
+
+# --------------------------------------------------------------- SSIM (Eq. 9)
+
+def _ssim_inputs(V, W, H, seed, smooth):
+    rng = np.random.default_rng(seed)
+    if smooth:      # render-like: low local variance, where the moments cancel most
+        yy, xx = np.mgrid[0:H, 0:W]
+        base = np.stack([0.5 + 0.3 * np.sin(xx / (7.0 + c) + v) * np.cos(yy / (5.0 + c))
+                         for v in range(V) for c in range(3)]).reshape(V, 3, H, W)
+        img = base + rng.normal(0, 0.005, base.shape)
+    else:
+        img = rng.uniform(0, 1, (V, 3, H, W))
+    tgt = np.clip(img + rng.normal(0, 0.03, img.shape), 0, 1)
+    dep = rng.uniform(1, 4, (V, H, W))
+    tgd = dep + rng.normal(0, 0.05, dep.shape)
+    tgd[:, : max(1, H // 5)] = 0.0
+    tgd[V - 1] = 0.0 if V > 1 else tgd[V - 1]      # the last view has no valid depth
+    f = lambda a: np.ascontiguousarray(a, np.float32)   # noqa: E731
+    return f(img), f(tgt), f(dep), f(tgd)
+
+
+def _gpu_ssim(N, img, tgt, dep, tgd, weights, lam):
+    import torch
+    V, _, H, W = img.shape
+    cfg = N.make_config(W, H, 16, 64, 0, 0.2, (0.0, 0.0, 0.0), 0.1)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()   # noqa: E731
+    cnt = (tgd > 0).reshape(V, -1).sum(1).astype(np.int32)
+    loss = torch.zeros(V, device="cuda")
+    gi = torch.full((V, 3, H, W), float("nan"), device="cuda")
+    gd = torch.full((V, H, W), float("nan"), device="cuda")
+    ws = torch.empty(N.cgs_ssim_workspace(V, cfg), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    N.cgs_ssim_loss(t(img), t(tgt), t(dep), t(tgd), t(cnt), V, cfg, t(np.float32(weights)), lam, loss, gi, gd, ws,
+                    st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    return loss.cpu().numpy(), gi.cpu().numpy().astype(np.float64), gd.cpu().numpy().astype(np.float64)
+
+
+def _check_grad(got, ref, what):
+    e_rel = rel_l2(got, ref)
+    e_max = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-30)
+    print(f"[ssim {what}] rel_l2 {e_rel:.1e} max/max {e_max:.1e}")
+    assert e_rel < GRAD_REL_TOL and e_max < GRAD_REL_TOL, (what, e_rel, e_max)
+
+
+@pytest.mark.parametrize("W,H,V,smooth", [(77, 45, 3, False), (77, 45, 3, True), (5, 3, 2, False),
+                                          (1, 1, 1, False), (33, 64, 2, True)])
+@pytest.mark.parametrize("lam", [0.0, 0.2, 1.0])
+def test_ssim_loss_matches_oracle(W, H, V, smooth, lam):
+    """Loss of Eq. 9 and its pixel gradients (tiles of 32 with ragged tails, images smaller
+    than the window, a view without valid depth) against the oracle on the same inputs."""
+    N = native()
+    img, tgt, dep, tgd = _ssim_inputs(V, W, H, seed=W * H + V, smooth=smooth)
+    w = np.array([1.0, 2.5, 0.5][:V])
+    loss, gi, gd = _gpu_ssim(N, img, tgt, dep, tgd, w, lam)
+    lo, gio, gdo = O.photometric_loss(img, dep, tgt, tgd, w, lam, 0.1)
+    np.testing.assert_allclose(loss, lo, rtol=2e-5, atol=2e-6)
+    _check_grad(gi, gio, f"img {W}x{H} lam {lam}")
+    np.testing.assert_allclose(gd, gdo, rtol=1e-6, atol=0)
+
+
+def test_ssim_loss_full_size_sampled_views():
+    """16 views at 1200x680 in one call (the windowed workload's launch); the oracle checks
+    the first and the last view."""
+    N = native()
+    V, W, H = 16, 1200, 680
+    img, tgt, dep, tgd = _ssim_inputs(V, W, H, seed=5, smooth=True)
+    w = np.linspace(0.5, 2.0, V)
+    loss, gi, gd = _gpu_ssim(N, img, tgt, dep, tgd, w, 0.2)
+    for v in (0, V - 1):
+        lo, gio, gdo = O.photometric_loss(img[v:v + 1], dep[v:v + 1], tgt[v:v + 1], tgd[v:v + 1], w[v:v + 1],
+                                          0.2, 0.1)
+        np.testing.assert_allclose(loss[v], lo[0], rtol=2e-5)
+        _check_grad(gi[v:v + 1], gio, f"full view {v}")
+        np.testing.assert_allclose(gd[v:v + 1], gdo, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("name", ["cfg1", "tiny_sh3_3views", "path_sh3_3views"])
+def test_window_ssim_iteration_matches_oracle(name):
+    """The window iteration with lambda_ssim = 0.2 (Eq. 9) against the oracle's."""
+    torch = torch_cuda()
+    native()
+    from paper_2410_00486_gb300.window import MappingWindow
+    sc, tgt_rgb, tgt_d = scene(name)
+    params, cams = gpu_scene_tensors(sc)
+    win = MappingWindow(params.clone(), sc.n, sc.sh_degree, sc.width, sc.height, sc.views, tile=sc.tile,
+                        batch_depth=64, lambda_ssim=0.2)
+    win.set_window(cams, torch.from_numpy(tgt_rgb), torch.from_numpy(tgt_d),
+                   torch.from_numpy(np.ascontiguousarray(sc.cams[:, 16])))
+    win.fit_capacity()
+    win.forward()
+    win.backward()
+    torch.cuda.synchronize()
+    assert win.read_status()[0] == 0
+    it = O.iteration(sc.params, sc.n, sc.sh_degree, sc.cams, sc.width, sc.height, sc.tile, tgt_rgb, tgt_d,
+                     tol=1e-3, lambda_ssim=0.2)
+    np.testing.assert_allclose(win.loss_view.cpu().numpy(), it["loss_view"], rtol=1e-4)
+    gg = win.grads.cpu().numpy().astype(np.float64)
+    errs = {k: rel_l2(gg[sl], it["grads"][sl]) for k, sl in group_slices(sc.n, sc.sh_degree).items()}
+    print(f"[ssim iter {name}] " + " ".join(f"{k}:{e:.1e}" for k, e in errs.items()))
+    for k, e in errs.items():
+        assert e < GRAD_REL_TOL, (k, e)
+
+
+def test_ssim_batched_per_view_and_splat_agree():
+    torch = torch_cuda()
+    native()
+    from paper_2410_00486_gb300.window import MappingWindow
+    sc, tgt_rgb, tgt_d = scene("path_sh3_3views")
+    params, cams = gpu_scene_tensors(sc)
+    wins = {}
+    for kind in ("batched", "per_view", "splat"):
+        win = MappingWindow(params.clone(), sc.n, 3, sc.width, sc.height, sc.views, tile=16, batch_depth=64,
+                            lambda_ssim=0.2, backward="splat" if kind == "splat" else "pixel")
+        win.set_window(cams, torch.from_numpy(tgt_rgb), torch.from_numpy(tgt_d))
+        win.fit_capacity()
+        (win.step_per_view if kind == "per_view" else win.step)()
+        torch.cuda.synchronize()
+        assert win.read_status()[0] == 0
+        wins[kind] = win
+    a = wins["batched"]
+    for kind in ("per_view", "splat"):
+        b = wins[kind]
+        torch.testing.assert_close(a.loss_view, b.loss_view, rtol=1e-6, atol=0)
+        for k, sl in group_slices(sc.n, 3).items():
+            assert rel_l2(b.grads[sl].cpu().numpy(), a.grads[sl].cpu().numpy()) < 1e-4, (kind, k)
