@@ -11,6 +11,10 @@ numpy / plain Python, step by step from the paper:
   * opacity regularisation, Eqs. 10-11 (Sec. III-C.3)
   * Adam with the 3DGS hyper-parameters the paper keeps (Sec. IV-A)
   * adaptive optimisation scheduler, Eqs. 5-8 (Sec. III-C.2)
+  * adaptive density control (clone / split / prune, Sec. III-A.3, IV-A)
+  * the SSIM term and the full loss of Eq. 9 (Sec. III-C.3)
+  * geometric densification: point cloud -> initial Gaussians (Sec. III-A.3, III-B),
+    with the exact k-nearest-neighbour distances computed in C by brute force
 
 Parity status: every function here is pinned by tests/test_oracle_*.py
 (closed forms, invariants, finite differences, scipy's spherical harmonics,
@@ -64,6 +68,7 @@ def _load():
         lib.orc_preprocess_bwd.argtypes = [P, i64, i32, P, i32, i32, i32, i32, f64, P, P]
         lib.orc_densify_stats.argtypes = [P, P, i32, i64, i32, i32, P, P, P]
         lib.orc_sh_basis.argtypes = [i32, f64, f64, f64, P, P]
+        lib.orc_knn_mean_d2.argtypes = [P, i64, i32, P]
         lib.orc_render_pixels.argtypes = [P, P, P, i32, i32, i32, P, P, i64, f64, P, P, P, P, P]
         _lib = lib
     return _lib
@@ -476,3 +481,43 @@ def photometric_loss(img, depth, tgt_rgb, tgt_depth, weight, lambda_ssim, lambda
                 loss[v] += lambda_d * np.abs(r[v]).sum() / cnt[v]
                 g_dep[v] = lambda_d * np.sign(r[v]) / cnt[v]
     return w * loss, w[:, None, None, None] * g_img, w[:, None, None] * g_dep
+
+
+# ------------------------------------------------------- geometric densification
+
+SH_C0 = 0.28209479177387814      # Y_0^0 = 1 / (2 sqrt(pi))
+KNN_K = 3
+KNN_FLOOR = 1e-7
+INIT_OPACITY = 0.1
+
+
+def knn_mean_d2(xyz, k=KNN_K) -> np.ndarray:
+    """Mean squared distance of every point to its k nearest other points (brute force, C)."""
+    lib = _load()
+    x = _f64(xyz).reshape(-1, 3)
+    out = np.zeros(x.shape[0])
+    if lib.orc_knn_mean_d2(_p(x), x.shape[0], k, _p(out)) != 0:
+        raise ValueError("k out of range")
+    return out
+
+
+def gaussians_from_points(xyz, rgb, deg, init_opacity=INIT_OPACITY, k=KNN_K, floor=KNN_FLOOR) -> np.ndarray:
+    """Geometric densification (Sec. III-A.3, III-B): one Gaussian per point of a keyframe's
+    coloured point cloud, initialised as 3DGS does (the renderer the paper keeps):
+      mean = the point; log-scale = log sqrt(max(d2, floor)) on all three axes, d2 the mean
+      squared distance to the k = 3 nearest other points (exact here; reading);
+      rotation = identity (1, 0, 0, 0); opacity logit = logit(init_opacity);
+      SH DC = (rgb - 1/2) / Y_0^0 (so the degree-0 colour is rgb); higher bands 0.
+    Returns the flat parameter vector (float64) of the m new Gaussians."""
+    x = _f64(xyz).reshape(-1, 3)
+    c = _f64(rgb).reshape(-1, 3)
+    m = x.shape[0]
+    K = (deg + 1) ** 2
+    d2 = np.maximum(knn_mean_d2(x, k), floor)
+    logs = np.repeat(0.5 * np.log(d2)[:, None], 3, axis=1)
+    quats = np.zeros((m, 4))
+    quats[:, 0] = 1.0
+    opac = np.full(m, np.log(init_opacity / (1.0 - init_opacity)))
+    dc = (c - 0.5) / SH_C0
+    rest = np.zeros((m, K - 1, 3))
+    return np.concatenate([x.ravel(), logs.ravel(), quats.ravel(), opac, dc.ravel(), rest.ravel()])

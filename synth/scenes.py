@@ -295,3 +295,21 @@ def make_records(seed: int, views: int, n: int, W: int, H: int, cull_frac: float
     tie = rng.uniform(0, 1, m) < depth_ties
     z[tie] = z[0] if m else 1.0
     return u, v, radius, z
+
+
+def make_point_cloud(seed: int, m: int, dup_frac: float = 0.01, outliers: int = 2):
+    """A keyframe's coloured point cloud for geometric densification: m points of the
+    6x5x3 m room (surfaces and interior as the room scenes), float32 xyz and rgb in [0, 1].
+    A share of points repeats another point exactly (as quantised depth back-projects
+    neighbouring pixels onto one point), and a few lie far outside the room."""
+    rng = np.random.default_rng(seed)
+    xyz = _room_means(rng, m)
+    rgb = rng.uniform(0.0, 1.0, (m, 3))
+    nd = int(dup_frac * m) if m > 1 else 0
+    if nd:
+        src = rng.integers(0, m, nd)
+        dst = rng.integers(0, m, nd)
+        xyz[dst] = xyz[src]
+    for i in range(min(outliers, m)):
+        xyz[rng.integers(0, m)] = rng.uniform(-40.0, 40.0, 3)
+    return xyz.astype(np.float32), rgb.astype(np.float32)
