@@ -299,7 +299,9 @@ def main():
     st = win.read_status()
     if st[0] != 0:
         raise SystemExit(f"device status after timing: {st}")
-    launches_per_step = 12   # preprocess, memset, count, scan, scatter, sort x2, order, fwd, loss, bwd x2, adam
+    # preprocess, count, scan, scatter, sort x2, order, fwd, loss reduce, raster bwd, preprocess bwd, adam,
+    # step counter (the launch list of the captured iteration shows these 13 kernels per step)
+    launches_per_step = 13
     gpu_launches = args.steps * launches_per_step
 
     # --- plain per-view form (same math, one view at a time), also graph-captured

@@ -329,6 +329,29 @@ int cgs_densify_apply(const float *params, const float *m, const float *v, int64
                       float *v_out, void *stream);
 
 /*
+ * Geometric densification (Sec. III-A.3, III-B): the coloured point cloud of a new keyframe
+ * becomes initial Gaussians, initialised as in 3D Gaussian Splatting (the renderer the paper
+ * keeps): mean = the point; log-scale = log sqrt(max(d2, 1e-7)) on all three axes, d2 the
+ * mean squared distance to the 3 nearest other points (exact; min(3, n_points - 1) of them,
+ * none when n_points = 1); rotation (1, 0, 0, 0); opacity logit(init_opacity); SH DC
+ * (rgb - 1/2) / Y_0^0; higher bands 0.
+ * cgs_points_to_gaussians writes n + n_points Gaussians to params_out / m_out / v_out
+ * (layout of cgs_param_count(n + n_points, sh_degree)): Gaussians 0..n-1 copied from
+ * params / m / v (NULL allowed when n = 0), then point i as Gaussian n + i with zero Adam
+ * moments.  xyz, rgb: device float[n_points][3].  The workspace (cgs_points_workspace(n_points)
+ * bytes, 256-byte aligned) holds a uniform grid of the points' bounding box (about one cell
+ * per point of its volume, at most 128 cells per axis) and the point ids sorted by cell.
+ * Outputs must not alias inputs.  A non-finite coordinate sets CGS_ERR_NONFINITE in
+ * *status_dev (that point's outputs are then unspecified).
+ */
+size_t cgs_points_workspace(int64_t n_points);
+int cgs_points_to_gaussians(const float *params, const float *m, const float *v, int64_t n,
+                            int32_t sh_degree, const float *xyz, const float *rgb, int64_t n_points,
+                            float init_opacity, void *workspace, size_t workspace_bytes,
+                            float *params_out, float *m_out, float *v_out, int32_t *status_dev,
+                            void *stream);
+
+/*
  * cgs_ssim_loss -- the photometric loss of Eq. 9 with its SSIM term (Sec. III-C.3), plus the
  * depth term, and its pixel gradients for the blend backward (cgs_render_bwd /
  * cgs_raster_bwd / cgs_raster_bwd_splat with dl_dimg, dl_ddepth non-NULL):

@@ -810,34 +810,48 @@ int orc_render_pixels(const double *rec, const uint32_t *ranges, const uint32_t 
  * k' = min(k, m - 1) smallest |x_i - x_j|^2, j != i (0 when m = 1).  Duplicated points are
  * neighbours at distance 0.
  */
+static double knn_one(const double *xyz, int64_t m, int k, int64_t i)
+{
+    double best[16];
+    int nb = 0;
+    for (int64_t j = 0; j < m; j++) {
+        if (j == i) continue;
+        double dx = xyz[3 * j] - xyz[3 * i], dy = xyz[3 * j + 1] - xyz[3 * i + 1],
+               dz = xyz[3 * j + 2] - xyz[3 * i + 2];
+        double d = dx * dx + dy * dy + dz * dz;
+        /* keep the nb smallest, ascending */
+        if (nb < k) {
+            best[nb++] = d;
+        } else if (d < best[k - 1]) {
+            best[k - 1] = d;
+        } else {
+            continue;
+        }
+        for (int a = nb - 1; a > 0 && best[a] < best[a - 1]; a--) {
+            double t = best[a];
+            best[a] = best[a - 1];
+            best[a - 1] = t;
+        }
+    }
+    double s = 0.0;
+    for (int a = 0; a < nb; a++) s += best[a];
+    return nb ? s / nb : 0.0;
+}
+
 int orc_knn_mean_d2(const double *xyz, int64_t m, int k, double *out)
 {
     if (k < 1 || k > 16) return -1;
-    for (int64_t i = 0; i < m; i++) {
-        double best[16];
-        int nb = 0;
-        for (int64_t j = 0; j < m; j++) {
-            if (j == i) continue;
-            double dx = xyz[3 * j] - xyz[3 * i], dy = xyz[3 * j + 1] - xyz[3 * i + 1],
-                   dz = xyz[3 * j + 2] - xyz[3 * i + 2];
-            double d = dx * dx + dy * dy + dz * dz;
-            /* keep the nb smallest, ascending */
-            if (nb < k) {
-                best[nb++] = d;
-            } else if (d < best[k - 1]) {
-                best[k - 1] = d;
-            } else {
-                continue;
-            }
-            for (int a = nb - 1; a > 0 && best[a] < best[a - 1]; a--) {
-                double t = best[a];
-                best[a] = best[a - 1];
-                best[a - 1] = t;
-            }
-        }
-        double s = 0.0;
-        for (int a = 0; a < nb; a++) s += best[a];
-        out[i] = nb ? s / nb : 0.0;
+    for (int64_t i = 0; i < m; i++) out[i] = knn_one(xyz, m, k, i);
+    return 0;
+}
+
+/* The same for the listed points only (idx[s]), for sampled checks of large clouds. */
+int orc_knn_mean_d2_at(const double *xyz, int64_t m, int k, const int64_t *idx, int64_t s, double *out)
+{
+    if (k < 1 || k > 16) return -1;
+    for (int64_t t = 0; t < s; t++) {
+        if (idx[t] < 0 || idx[t] >= m) return -2;
+        out[t] = knn_one(xyz, m, k, idx[t]);
     }
     return 0;
 }

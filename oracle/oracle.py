@@ -69,6 +69,7 @@ def _load():
         lib.orc_densify_stats.argtypes = [P, P, i32, i64, i32, i32, P, P, P]
         lib.orc_sh_basis.argtypes = [i32, f64, f64, f64, P, P]
         lib.orc_knn_mean_d2.argtypes = [P, i64, i32, P]
+        lib.orc_knn_mean_d2_at.argtypes = [P, i64, i32, P, i64, P]
         lib.orc_render_pixels.argtypes = [P, P, P, i32, i32, i32, P, P, i64, f64, P, P, P, P, P]
         _lib = lib
     return _lib
@@ -498,6 +499,17 @@ def knn_mean_d2(xyz, k=KNN_K) -> np.ndarray:
     out = np.zeros(x.shape[0])
     if lib.orc_knn_mean_d2(_p(x), x.shape[0], k, _p(out)) != 0:
         raise ValueError("k out of range")
+    return out
+
+
+def knn_mean_d2_at(xyz, idx, k=KNN_K) -> np.ndarray:
+    """knn_mean_d2 for the listed point indices only (brute force over the whole cloud)."""
+    lib = _load()
+    x = _f64(xyz).reshape(-1, 3)
+    ii = np.ascontiguousarray(idx, np.int64)
+    out = np.zeros(ii.size)
+    if lib.orc_knn_mean_d2_at(_p(x), x.shape[0], k, _p(ii), ii.size, _p(out)) != 0:
+        raise ValueError("k or an index out of range")
     return out
 
 

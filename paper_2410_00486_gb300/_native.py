@@ -78,6 +78,9 @@ _SIGS = {
     "cgs_densify_plan": (c_int32, [_P, c_int64, c_int32, _P, _P, c_double, c_double, c_double, _P, c_size_t, _P,
                                    _P]),
     "cgs_densify_apply": (c_int32, [_P, _P, _P, c_int64, c_int32, _P, c_size_t, _P, c_int64, _P, _P, _P, _P]),
+    "cgs_points_workspace": (c_size_t, [c_int64]),
+    "cgs_points_to_gaussians": (c_int32, [_P, _P, _P, c_int64, c_int32, _P, _P, c_int64, c_float, _P, c_size_t, _P,
+                                          _P, _P, _P, _P]),
     "cgs_ssim_workspace": (c_size_t, [c_int32, _P]),
     "cgs_ssim_loss": (c_int32, [_P, _P, _P, _P, _P, c_int32, _P, _P, c_float, _P, _P, _P, _P, c_size_t, _P,
                                 _P]),
@@ -276,6 +279,18 @@ def cgs_densify_apply(params, m, v, n, sh_degree, workspace, normals, n_out, par
                                                         _dev(workspace), nbytes, _dev(normals), n_out,
                                                         _dev(params_out), _dev(m_out), _dev(v_out),
                                                         _stream(stream)))
+
+
+def cgs_points_workspace(n_points) -> int:
+    return lib().cgs_points_workspace(n_points)
+
+
+def cgs_points_to_gaussians(params, m, v, n, sh_degree, xyz, rgb, n_points, init_opacity, workspace, params_out,
+                            m_out, v_out, status=None, stream=None):
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check("cgs_points_to_gaussians", lib().cgs_points_to_gaussians(
+        _dev(params), _dev(m), _dev(v), n, sh_degree, _dev(xyz), _dev(rgb), n_points, float(init_opacity),
+        _dev(workspace), nbytes, _dev(params_out), _dev(m_out), _dev(v_out), _dev(status), _stream(stream)))
 
 
 def cgs_ssim_workspace(V, cfg) -> int:

@@ -228,6 +228,29 @@ class MappingWindow:
         self._resize(n_out, p2, m2, v2)
         return {"pruned": counts[0], "kept": counts[1], "cloned": counts[2], "split": counts[3], "n": n_out}
 
+    def add_points(self, xyz: torch.Tensor, rgb: torch.Tensor, init_opacity: float = 0.1) -> int:
+        """Geometric densification (Sec. III-A.3, III-B): append one Gaussian per point of a new
+        keyframe's coloured point cloud (xyz, rgb: float32 [m, 3] on the device), initialised
+        from the exact 3-nearest-neighbour distances; existing Gaussians keep their Adam state.
+        Reallocates every per-Gaussian buffer (a captured graph is dropped).  Returns the new
+        Gaussian count."""
+        xyz = xyz.to(self.device, torch.float32).contiguous()
+        rgb = rgb.to(self.device, torch.float32).contiguous()
+        mpts = int(xyz.shape[0])
+        if xyz.shape != (mpts, 3) or rgb.shape != (mpts, 3):
+            raise ValueError("xyz and rgb must be [m, 3]")
+        if mpts == 0:
+            return self.n
+        n_out = self.n + mpts
+        P2 = N.cgs_param_count(n_out, self.sh_degree)
+        f32 = dict(dtype=torch.float32, device=self.device)
+        p2, m2, v2 = torch.empty(P2, **f32), torch.empty(P2, **f32), torch.empty(P2, **f32)
+        ws = torch.empty(N.cgs_points_workspace(mpts), dtype=torch.uint8, device=self.device)
+        N.cgs_points_to_gaussians(self.params, self.m, self.v, self.n, self.sh_degree, xyz, rgb, mpts, init_opacity,
+                                  ws, p2, m2, v2, self.status)
+        self._resize(n_out, p2, m2, v2)
+        return n_out
+
     def _resize(self, n: int, params: torch.Tensor, m: torch.Tensor, v: torch.Tensor):
         f32 = dict(dtype=torch.float32, device=self.device)
         self.n = int(n)

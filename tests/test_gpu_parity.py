@@ -791,3 +791,129 @@ def test_ssim_batched_per_view_and_splat_agree():
         torch.testing.assert_close(a.loss_view, b.loss_view, rtol=1e-6, atol=0)
         for k, sl in group_slices(sc.n, 3).items():
             assert rel_l2(b.grads[sl].cpu().numpy(), a.grads[sl].cpu().numpy()) < 1e-4, (kind, k)
+
+
+# ----------------------------------------------------- geometric densification
+
+def _gpu_points(N, xyz, rgb, deg, prefix=None):
+    import torch
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()   # noqa: E731
+    m = xyz.shape[0]
+    n = 0 if prefix is None else prefix[0]
+    P2 = N.cgs_param_count(n + m, deg)
+    p2, m2, v2 = (torch.full((P2,), float("nan"), device="cuda") for _ in range(3))
+    ws = torch.empty(max(256, N.cgs_points_workspace(m)), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    args = (None, None, None) if prefix is None else tuple(t(a) for a in prefix[1:])
+    N.cgs_points_to_gaussians(*args, n, deg, t(xyz), t(rgb), m, 0.1, ws, p2, m2, v2, st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    return p2.cpu().numpy(), m2.cpu().numpy(), v2.cpu().numpy()
+
+
+def _check_new_gaussians(got, xyz, rgb, deg, n, d2_ref, idx=None):
+    from synth.scenes import param_layout
+    m = xyz.shape[0]
+    nt = n + m
+    lay = param_layout(nt, deg)
+    K = (deg + 1) ** 2
+    sel = np.arange(m) if idx is None else np.asarray(idx)
+    rows = n + sel
+    np.testing.assert_array_equal(got[: 3 * nt].reshape(nt, 3)[rows], xyz[sel])
+    logs = got[lay["log_scales"]: lay["quats"]].reshape(nt, 3)[rows]
+    expect = 0.5 * np.log(np.maximum(d2_ref, 1e-7))
+    e = np.abs(logs - expect[:, None]).max()
+    print(f"[points m={m} n={n}] max |dlog s| {e:.2e}")
+    assert e < 2e-6, e
+    q = got[lay["quats"]: lay["opacity"]].reshape(nt, 4)[rows]
+    assert np.all(q == np.array([1, 0, 0, 0], np.float32))
+    np.testing.assert_allclose(got[lay["opacity"]: lay["sh_dc"]][rows], np.log(0.1 / 0.9), rtol=1e-6)
+    dc = got[lay["sh_dc"]: lay["sh_rest"]].reshape(nt, 3)[rows]
+    np.testing.assert_allclose(dc, (rgb[sel].astype(np.float64) - 0.5) / O.SH_C0, rtol=1e-6, atol=1e-6)
+    rest = got[lay["sh_rest"]:].reshape(nt, 3 * (K - 1))[rows]
+    assert np.all(rest == 0)
+
+
+@pytest.mark.parametrize("m,dup,deg", [(1, 0.0, 0), (2, 0.0, 1), (4, 0.0, 3), (60, 0.5, 0), (1500, 0.05, 3),
+                                       (20000, 0.01, 3)])
+def test_points_to_gaussians_matches_oracle(m, dup, deg):
+    """Exact 3-NN scales, identity rotations, opacity 0.1 and SH DC from the colours, for
+    clouds from one point up to 20k points with exact duplicates and far outliers."""
+    from synth import make_point_cloud
+    N = native()
+    xyz, rgb = make_point_cloud(m, m, dup_frac=dup)
+    got, gm, gv = _gpu_points(N, xyz, rgb, deg)
+    _check_new_gaussians(got, xyz, rgb, deg, 0, O.knn_mean_d2(xyz))
+    assert np.all(gm == 0) and np.all(gv == 0)
+
+
+def test_points_appended_after_existing_gaussians():
+    from synth import make_point_cloud
+    N = native()
+    sc = make_scene(3, n=3000)
+    rng = np.random.default_rng(2)
+    P = sc.params
+    M = rng.normal(size=P.size).astype(np.float32)
+    Vv = rng.uniform(0, 1, P.size).astype(np.float32)
+    xyz, rgb = make_point_cloud(9, 5000)
+    got, gm, gv = _gpu_points(N, xyz, rgb, sc.sh_degree, (sc.n, P, M, Vv))
+    n, mp, deg = sc.n, xyz.shape[0], sc.sh_degree
+    K = (deg + 1) ** 2
+    widths = [3, 3, 4, 1, 3, 3 * (K - 1)]
+    oi = oo = 0
+    for w in widths:      # the existing Gaussians are copied group by group, moments included
+        for src, dst in ((P, got), (M, gm), (Vv, gv)):
+            np.testing.assert_array_equal(dst[oo: oo + w * n], src[oi: oi + w * n])
+        assert np.all(gm[oo + w * n: oo + w * (n + mp)] == 0) and np.all(gv[oo + w * n: oo + w * (n + mp)] == 0)
+        oi += w * n
+        oo += w * (n + mp)
+    _check_new_gaussians(got, xyz, rgb, deg, n, O.knn_mean_d2(xyz))
+
+
+@pytest.mark.parametrize("shape", ["flat", "line"])
+def test_points_degenerate_clouds(shape):
+    N = native()
+    rng = np.random.default_rng(4)
+    xyz = rng.uniform(-1, 1, (3000, 3)).astype(np.float32)
+    if shape == "flat":
+        xyz[:, 1] = 0.25
+    else:
+        xyz[:, 1:] = 0.0
+    rgb = rng.uniform(0, 1, xyz.shape).astype(np.float32)
+    got, _, _ = _gpu_points(N, xyz, rgb, 0)
+    _check_new_gaussians(got, xyz, rgb, 0, 0, O.knn_mean_d2(xyz))
+
+
+def test_points_full_size_sampled():
+    """A 300k-point keyframe cloud (a 1200x680 RGB-D frame back-projected at about every
+    third pixel); the oracle checks 400 sampled points by brute force over the whole cloud."""
+    from synth import make_point_cloud
+    N = native()
+    xyz, rgb = make_point_cloud(11, 300000, dup_frac=0.01, outliers=5)
+    got, _, _ = _gpu_points(N, xyz, rgb, 3)
+    idx = np.random.default_rng(0).choice(xyz.shape[0], 400, replace=False)
+    _check_new_gaussians(got, xyz, rgb, 3, 0, O.knn_mean_d2_at(xyz, idx), idx)
+
+
+def test_window_add_points_then_iterate():
+    torch = torch_cuda()
+    native()
+    from synth import make_point_cloud
+    from paper_2410_00486_gb300.window import MappingWindow
+    sc, tgt_rgb, tgt_d = scene("cfg3")
+    params, cams = gpu_scene_tensors(sc)
+    win = MappingWindow(params.clone(), sc.n, sc.sh_degree, sc.width, sc.height, 1, tile=16)
+    win.set_window(cams, torch.from_numpy(tgt_rgb), torch.from_numpy(tgt_d))
+    win.fit_capacity(2.0)
+    win.step()
+    xyz, rgb = make_point_cloud(12, 2000)
+    xyz = xyz * np.float32(0.3) + np.array([0.0, 0.0, 2.5], np.float32)     # in front of the camera
+    n0 = win.n
+    assert win.add_points(torch.from_numpy(xyz), torch.from_numpy(rgb)) == n0 + 2000
+    torch.testing.assert_close(win.params[: 3 * n0].cpu(), params[: 3 * n0].cpu(), rtol=1e-2, atol=1e-2)
+    win.fit_capacity(2.0)
+    for _ in range(2):
+        win.step()
+    torch.cuda.synchronize()
+    assert win.read_status()[0] == 0
+    assert torch.isfinite(win.params).all()

@@ -70,3 +70,11 @@ def test_gaussians_from_points_floor_for_duplicates():
     np.testing.assert_allclose(p[15:30], 0.5 * np.log(1e-7))
     with pytest.raises(ValueError):
         O.knn_mean_d2(xyz, k=0)
+
+
+def test_sampled_knn_equals_full():
+    xyz, _ = make_point_cloud(8, 800, dup_frac=0.05)
+    idx = np.array([0, 5, 799, 400, 5])
+    np.testing.assert_array_equal(O.knn_mean_d2_at(xyz, idx), O.knn_mean_d2(xyz)[idx])
+    with pytest.raises(ValueError):
+        O.knn_mean_d2_at(xyz, [800])
