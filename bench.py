@@ -363,7 +363,12 @@ def main():
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e2e["value"] = world * e2e["steps"] / float(tt.item())
 
-    roof = roofline(stages, work, clk.summary()) if stages else None
+    roof = None
+    if stages:
+        work["workload"] = workload_config(sc)["workload"]
+        roof = roofline(stages, work, clk.summary())
+        roof["iteration_bound_ms"] = round(iteration_bound_ms(stages, work), 4)
+        roof["iteration_frac"] = roof["iteration_bound_ms"] / (ms_max / args.steps)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sc)
@@ -512,11 +517,60 @@ def stage_breakdown(win, N, reps=5):
     rad = win.rec.view(torch.int32).view(-1, 12)[:, 7]
     work = {
         "pairs_fwd_eval": float(part[:, 3].sum()), "pairs_blend": float(part[:, 4].sum()),
-        "pairs_bwd_eval": float(win.last.double().sum()),
+        "pairs_bwd_eval": backward_pairs(win.rec, win.vals, win.ranges, win.last, win.V, win.W, win.H,
+                                         win.cfg.tile, int(win.n_inst.item())),
+        "sum_last": float(win.last.double().sum()),
         "visible_slots": int((rad > 0).sum().item()), "instances": int(win.n_inst.item()),
         "params": win.P, "n": win.n, "slots": win.V * win.n, "pixels": win.V * win.W * win.H, "tiles": win.Ttot,
     }
     return {k: round(v, 4) for k, v in acc.items()}, work
+
+
+def staging_pass(rec, bx0, bx1, by0, by1):
+    """The raster kernels' staging test (a splat is kept if its 1/255 iso-ellipse's bounding
+    box can reach the tile's pixel-centre box), in float32 on the records [k, 12]."""
+    import torch
+    u, v, A, Bc, C, o = (rec[:, i] for i in range(6))
+    keep = o * 255.0 >= 0.9999
+    det = A * C - Bc * Bc
+    t2 = 2.0 * torch.log(255.0 * o) * 1.001 + 1e-3
+    ex = torch.sqrt(t2 * C / det) + 1e-2
+    ey = torch.sqrt(t2 * A / det) + 1e-2
+    dx = (u - torch.minimum(torch.maximum(u, bx0), bx1)).abs()
+    dy = (v - torch.minimum(torch.maximum(v, by0), by1)).abs()
+    return keep & (~(det > 0) | ((dx <= ex) & (dy <= ey)))
+
+
+def backward_pairs(rec, vals, ranges, last, V, W, H, B, n_inst, chunk=1 << 23):
+    """(pixel, splat) pairs the raster backward evaluates: for every pixel, the splats of its
+    tile's list before its `last` position that pass the staging test.  A prefix sum of the
+    pass flags over the tile lists turns this into one gather per pixel (measurement only)."""
+    import torch
+    dev = rec.device
+    Tx, Ty = -(-W // B), -(-H // B)
+    rg = ranges.view(-1, 2).long() & 0xFFFFFFFF
+    start, end = rg[:, 0], rg[:, 1]
+    recs = rec.view(-1, 12)
+    ids = vals[:n_inst].long() & 0xFFFFFFFF
+    tile_of = torch.repeat_interleave(torch.arange(rg.shape[0], device=dev), end - start)
+    passed = torch.empty(n_inst, dtype=torch.int64, device=dev)
+    for c0 in range(0, n_inst, chunk):
+        c1 = min(n_inst, c0 + chunk)
+        t = tile_of[c0:c1] % (Tx * Ty)
+        tx, ty = t % Tx, t // Tx
+        bx0 = (tx * B).float()
+        bx1 = (torch.clamp(tx * B + B, max=W) - 1).float()
+        by0 = (ty * B).float()
+        by1 = (torch.clamp(ty * B + B, max=H) - 1).float()
+        passed[c0:c1] = staging_pass(recs[ids[c0:c1]], bx0, bx1, by0, by1).long()
+    cum = torch.zeros(n_inst + 1, dtype=torch.int64, device=dev)
+    cum[1:] = torch.cumsum(passed, 0)
+    yy, xx = torch.meshgrid(torch.arange(H, device=dev), torch.arange(W, device=dev), indexing="ij")
+    tpix = (yy // B) * Tx + (xx // B)
+    tglob = (torch.arange(V, device=dev)[:, None, None] * (Tx * Ty) + tpix[None]).reshape(-1)
+    st = start[tglob]
+    lst = last.reshape(-1).long()
+    return float((cum[st + lst] - cum[st]).sum().item())
 
 
 def hbm_bytes(stage, w):
@@ -531,6 +585,50 @@ def hbm_bytes(stage, w):
     if stage == "adam":
         return 28 * P
     return None
+
+
+TRAFFIC_PROFILE = ROOT / "profiles" / "k_render_bwd_traffic_window16_300k_1200x680.md"
+RASTER_BWD_SOURCES = ("render_bwd.cu", "raster.cuh", "cgs_internal.cuh")
+
+
+def raster_bwd_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in RASTER_BWD_SOURCES:
+        h.update((ROOT / "paper_2410_00486_gb300" / "csrc" / f).read_bytes())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch of k_render_bwd from the committed ncu capture, if it was taken on
+    this workload and the kernel's sources are unchanged since (else None)."""
+    if not TRAFFIC_PROFILE.exists():
+        return None
+    kv = {}
+    for line in TRAFFIC_PROFILE.read_text().splitlines():
+        if line.startswith("- ") and ": " in line:
+            k, v = line[2:].split(": ", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("source_sha256") != raster_bwd_source_hash() or kv.get("workload") != workload:
+        return None
+    return float(kv["traffic_bytes_per_launch"])
+
+
+def iteration_bound_ms(stages, work):
+    """Time one iteration would take if every stage ran at its roofline: HBM stages at the
+    measured copy bandwidth, raster stages at the FP32 lane peak (SURVEY-style combined bound)."""
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    bw = peaks.get("hbm_gbs", 6800.0) * 1e9
+    alu = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    t = 0.0
+    for st in stages:
+        if st == "render_fwd":
+            t += (FWD_OPS_EVAL * work["pairs_fwd_eval"] + FWD_OPS_BLEND * work["pairs_blend"]) / alu
+        elif st == "raster_bwd":
+            t += (BWD_OPS_EVAL * work["pairs_bwd_eval"] + BWD_OPS_BLEND * work["pairs_blend"]) / alu
+        else:
+            t += hbm_bytes(st, work) / bw
+    return 1e3 * t
 
 
 def roofline(stages, work, clocks):
@@ -549,10 +647,13 @@ def roofline(stages, work, clocks):
             ops = BWD_OPS_EVAL * work["pairs_bwd_eval"] + BWD_OPS_BLEND * work["pairs_blend"]
         peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
         ach = ops / t / 1e12
+        traffic = recorded_traffic(work.get("workload")) if dom == "raster_bwd" else None
         return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Top/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (FP32 instructions/s)",
-                "work": {k: work[k] for k in ("pairs_fwd_eval", "pairs_bwd_eval", "pairs_blend")}}
+                "frac": ach / peak, "traffic": traffic,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (FP32 instructions/s), derived",
+                "work": {k: work[k] for k in ("pairs_fwd_eval", "pairs_bwd_eval", "pairs_blend", "sum_last")},
+                "ops_per_pair": {"fwd_eval": FWD_OPS_EVAL, "fwd_blend": FWD_OPS_BLEND, "bwd_eval": BWD_OPS_EVAL,
+                                 "bwd_blend": BWD_OPS_BLEND}}
     b = hbm_bytes(dom, work)
     peak = peaks.get("hbm_gbs", 6800.0)
     ach = b / t / 1e9
