@@ -129,11 +129,24 @@ __device__ __forceinline__ void stage_splat(const float4 &r0, const float4 &r1, 
 }
 
 // Exponent of the projected Gaussian at a pixel from a staged splat, with explicit
-// roundings so both raster kernels compute the same bits:
-//   power = dx (-A/2 dx - B dy) + (-C/2 dy) dy,  dx = u - x, dy = v - y.
+// roundings so every raster kernel computes the same bits:
+//   power = (-A/2 dx) dx + dy ((-C/2) dy + (-B) dx),  dx = u - x, dy = v - y.
+// The dx terms are shared by the pixels of a column: power_x gives them once, and
+// power_at finishes a pixel with two fused multiply-adds.
+struct PowerX {
+    float a, b;   // (-A/2 dx) dx and (-B) dx
+};
+__device__ __forceinline__ PowerX power_x(const float4 &t0, float dx)
+{
+    return PowerX{__fmul_rn(__fmul_rn(t0.z, dx), dx), __fmul_rn(t0.w, dx)};
+}
+__device__ __forceinline__ float power_at(const PowerX &x, float hC, float dy)
+{
+    return fmaf(dy, fmaf(hC, dy, x.b), x.a);
+}
 __device__ __forceinline__ float staged_power(const float4 &t0, float hC, float dx, float dy)
 {
-    return fmaf(dx, fmaf(t0.z, dx, __fmul_rn(t0.w, dy)), __fmul_rn(__fmul_rn(hC, dy), dy));
+    return power_at(power_x(t0, dx), hC, dy);
 }
 
 cudaError_t raster_fwd(const RasterFwdArgs &a, int B, int BD, cudaStream_t s);

@@ -1,19 +1,23 @@
 // Backward of the blend (Eqs. 2-4, Sec. III-C.1, CaRtGS), pixel-parallel.
 //
-// One block per (view, tile), two vertically adjacent pixels per thread, walking the
-// tile's list back to front from the block's largest `last`.  Staging applies the
-// forward's tile test and exponent threshold, so the same splats are considered.  Each pixel recomputes alpha exactly as
-// the forward did (same rounding, same decisions) and its transmittance from the
-// stored final T, T_j = T_{j+1} / (1 - alpha_j), so no per-pixel splat list is kept.
-// The accumulated colour behind splat j follows acc_j = a_{j+1} c_{j+1} +
-// (1 - a_{j+1}) acc_{j+1}, and
-//   dL/dalpha_j = T_j sum_c gI_c (c_j - acc_j) + T_j gD (z_j - accD_j)
-//                 - T_final (bg . gI) / (1 - alpha_j).
-// The per-(splat, pixel) gradients of a thread's two pixels are added in registers,
-// then the 64 pixels of a warp are summed with a butterfly reduce-scatter (15 shuffles
-// for 10 fields instead of 50 for a plain tree per field), after which ten lanes each
-// issue one atomic add into the slot's gradient record.  Warps where no pixel blended
-// the splat skip it (vote).
+// One block per (view, tile), four vertically adjacent pixels per thread (two on 8x8
+// tiles), walking the tile's list back to front from the block's largest `last`.
+// Staging applies the forward's tile test and exponent threshold, so the same splats
+// are considered.  Each pixel recomputes alpha exactly as the forward did (same
+// rounding, same decisions) and its transmittance from the stored final T,
+// T_j = T_{j+1} / (1 - alpha_j), so no per-pixel splat list is kept.
+//
+// With R_j the colour behind splat j normalised by the transmittance just after it,
+// R_last = bg and R_{j-1} = a_j c_j + (1 - a_j) R_j (depth alike, starting at 0),
+//   dL/dalpha_j = T_j [ gI . (c_j - R_j) + gD (z_j - Rz_j) ],
+// so a pixel only carries the scalar S_j = gI . R_j + gD Rz_j, updated by the same
+// recursion with c_j . gI + z_j gD in place of the colour.
+//
+// The per-(splat, pixel) gradients of a thread's pixels are added in registers (the
+// pixels share dx, so the dx moments are formed once per thread), then a warp's pixels
+// are summed with a butterfly reduce-scatter (15 shuffles for 10 fields instead of 50
+// for a plain tree per field), after which ten lanes each issue one atomic add into
+// the slot's gradient record.  Warps where no pixel blended the splat skip it (vote).
 #include "raster.cuh"
 
 namespace cgs {
@@ -77,9 +81,10 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>()) k_render_bwd(Ras
     const uint32_t len = a.ranges[2 * tile + 1] - start;
     const size_t HW = (size_t)a.g.W * a.g.H;
 
-    // per-pixel state
-    float fy[PPT], T[PPT], gI0[PPT], gI1[PPT], gI2[PPT], gD[PPT], bgdot[PPT];
-    float acc0[PPT], acc1[PPT], acc2[PPT], accD[PPT];
+    // per-pixel state: transmittance, pixel gradients, and S = (colour behind) . gI +
+    // (depth behind) gD, where "behind" starts as the background (no depth) and follows
+    // R <- alpha c + (1 - alpha) R towards the front
+    float fy[PPT], T[PPT], gI0[PPT], gI1[PPT], gI2[PPT], gD[PPT], S[PPT];
     uint32_t lst[PPT];
     uint32_t m = 0;
 #pragma unroll
@@ -88,8 +93,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>()) k_render_bwd(Ras
         fy[p] = (float)py;
         lst[p] = 0;
         T[p] = 1.f;
-        gI0[p] = gI1[p] = gI2[p] = gD[p] = bgdot[p] = 0.f;
-        acc0[p] = acc1[p] = acc2[p] = accD[p] = 0.f;
+        gI0[p] = gI1[p] = gI2[p] = gD[p] = S[p] = 0.f;
         if (!(px < a.g.W && py < a.g.H)) continue;
         const size_t q = (size_t)py * a.g.W + px;
         const size_t pix = (size_t)view * HW + q;
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>()) k_render_bwd(Ras
                 if (td > 0.f && cnt > 0) gD[p] = w * a.lambda_d * sgnf(a.depth[pix] - td) / (float)cnt;
             }
         }
-        bgdot[p] = T[p] * (a.bg0 * gI0[p] + a.bg1 * gI1[p] + a.bg2 * gI2[p]);
+        S[p] = a.bg0 * gI0[p] + a.bg1 * gI1[p] + a.bg2 * gI2[p];
         m = max(m, lst[p]);
     }
     // block-wide largest `last`: the walk starts there
@@ -165,15 +169,16 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>()) k_render_bwd(Ras
             const float4 q0 = s0[j];
             const float4 q1 = s1[j];
             const float dx = __fsub_rn(q0.x, fx);
-            float v[16];
-#pragma unroll
-            for (int k = 0; k < 16; k++) v[k] = 0.f;
+            const PowerX pxs = power_x(q0, dx);
+            // per-thread sums over its pixels: colour / depth / opacity gradients, and the
+            // moments sum dp, sum dp dy, sum dp dy^2 of dp = dL/dpower (dx is shared)
+            float gr = 0.f, gg = 0.f, gb = 0.f, gz = 0.f, go = 0.f, sdp = 0.f, sdpy = 0.f, sdpyy = 0.f;
             bool contrib = false;
 #pragma unroll
             for (int p = 0; p < PPT; p++) {
                 if (!(pos < lst[p])) continue;
                 const float dy = __fsub_rn(q0.y, fy[p]);
-                const float power = staged_power(q0, q1.x, dx, dy);
+                const float power = power_at(pxs, q1.x, dy);
                 if (power > 0.f || power < q1.w) continue;
                 const float G = __expf(power);
                 const float araw = __fmul_rn(q1.y, G);
@@ -183,54 +188,63 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>()) k_render_bwd(Ras
                 const float inv_om = __fdividef(1.f, __fsub_rn(1.f, alpha));
                 T[p] = T[p] * inv_om;                             // transmittance before splat j
                 const float wT = alpha * T[p];
-                v[8] += wT * gI0[p];
-                v[9] += wT * gI1[p];
-                v[10] += wT * gI2[p];
-                v[6] += wT * gD[p];
-                // acc = colour (and depth) accumulated behind splat j, as seen just after it
-                float dLda = (q2.x - acc0[p]) * gI0[p] + (q2.y - acc1[p]) * gI1[p] + (q2.z - acc2[p]) * gI2[p] +
-                             (q1.z - accD[p]) * gD[p];
-                dLda = dLda * T[p] - bgdot[p] * inv_om;
-                // fold splat j in for the splats in front of it: acc <- a c + (1 - a) acc
-                acc0[p] = fmaf(alpha, q2.x - acc0[p], acc0[p]);
-                acc1[p] = fmaf(alpha, q2.y - acc1[p], acc1[p]);
-                acc2[p] = fmaf(alpha, q2.z - acc2[p], acc2[p]);
-                accD[p] = fmaf(alpha, q1.z - accD[p], accD[p]);
+                gr = fmaf(wT, gI0[p], gr);
+                gg = fmaf(wT, gI1[p], gg);
+                gb = fmaf(wT, gI2[p], gb);
+                gz = fmaf(wT, gD[p], gz);
+                // dL/dalpha = T (c . gI + z gD - S); then fold splat j into S for the
+                // splats in front of it
+                const float cg = fmaf(q1.z, gD[p], fmaf(q2.z, gI2[p], fmaf(q2.y, gI1[p], q2.x * gI0[p])));
+                const float diff = cg - S[p];
+                S[p] = fmaf(alpha, diff, S[p]);
                 if (!(araw > kAlphaMax)) {
-                    // dalpha/dpower = alpha, dalpha/dopacity = G.  Raw moments of
-                    // dp = dL/dpower are summed here; the conic / centre gradients are
-                    // formed from them once per warp after the reduction.
+                    // dalpha/dpower = alpha, dalpha/dopacity = G
+                    const float dLda = diff * T[p];
+                    go = fmaf(dLda, G, go);
                     const float dp = dLda * alpha;
-                    v[5] += dLda * G;
-                    const float dpx = dp * dx, dpy = dp * dy;
-                    v[0] += dpx;             // sum dp dx
-                    v[1] += dpy;             // sum dp dy
-                    v[2] += dpx * dx;        // sum dp dx^2
-                    v[3] += dpx * dy;        // sum dp dx dy
-                    v[4] += dpy * dy;        // sum dp dy^2
+                    const float dpy = dp * dy;
+                    sdp += dp;
+                    sdpy += dpy;
+                    sdpyy = fmaf(dpy, dy, sdpyy);
                 }
             }
             const unsigned who = __ballot_sync(kFull, contrib);
             if (who == 0u) continue;
+            // raw moments of dp over this thread's pixels: sum dp dx, dp dy, dp dx^2, dp dx dy, dp dy^2
+            const float m0 = sdp * dx, m3 = sdpy * dx;
             if ((who & (who - 1u)) == 0u) {
                 // a single contributing lane adds its sums directly
                 if (contrib) {
                     float *g = a.sgrad + (size_t)sslot[j] * 12;
-                    const float hA = s0[j].z, nB = s0[j].w, hC = s1[j].x;
-                    atomicAdd(g + 0, 2.f * hA * v[0] + nB * v[1]);
-                    atomicAdd(g + 1, 2.f * hC * v[1] + nB * v[0]);
-                    atomicAdd(g + 2, -0.5f * v[2]);
-                    atomicAdd(g + 3, -v[3]);
-                    atomicAdd(g + 4, -0.5f * v[4]);
-                    atomicAdd(g + 5, v[5]);
-                    atomicAdd(g + 6, v[6]);
-                    atomicAdd(g + 8, v[8]);
-                    atomicAdd(g + 9, v[9]);
-                    atomicAdd(g + 10, v[10]);
+                    const float hA = q0.z, nB = q0.w, hC = q1.x;
+                    atomicAdd(g + 0, 2.f * hA * m0 + nB * sdpy);
+                    atomicAdd(g + 1, 2.f * hC * sdpy + nB * m0);
+                    atomicAdd(g + 2, -0.5f * (m0 * dx));
+                    atomicAdd(g + 3, -m3);
+                    atomicAdd(g + 4, -0.5f * sdpyy);
+                    atomicAdd(g + 5, go);
+                    atomicAdd(g + 6, gz);
+                    atomicAdd(g + 8, gr);
+                    atomicAdd(g + 9, gg);
+                    atomicAdd(g + 10, gb);
                 }
                 continue;
             }
             {
+                float v[16];
+                v[0] = m0;
+                v[1] = sdpy;
+                v[2] = m0 * dx;
+                v[3] = m3;
+                v[4] = sdpyy;
+                v[5] = go;
+                v[6] = gz;
+                v[7] = 0.f;
+                v[8] = gr;
+                v[9] = gg;
+                v[10] = gb;
+#pragma unroll
+                for (int k = 11; k < 16; k++) v[k] = 0.f;
                 float sum = warp_reduce_scatter16(v, lane);
                 const int f = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
                 // fields 0 and 1 sit in lanes that differ in bit 1: exchange the two first moments
@@ -239,8 +253,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>()) k_render_bwd(Ras
                 //   dL/du = -(A S_dx + B S_dy), dL/dv = -(C S_dy + B S_dx),
                 //   dL/dA = -S_xx / 2, dL/dB = -S_xy, dL/dC = -S_yy / 2
                 // (staged q0.z = -A/2, q0.w = -B, q1.x = -C/2)
-                const float4 q0 = s0[j];
-                const float hC = s1[j].x;
+                const float hC = q1.x;
                 if (f == 0) sum = 2.f * q0.z * sum + q0.w * other;
                 else if (f == 1) sum = 2.f * hC * sum + q0.w * other;
                 else if (f == 2 || f == 4) sum = -0.5f * sum;

@@ -99,13 +99,12 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>()) k_render_fwd(Ras
                 }
                 const float4 q0 = s0[j];
                 const float4 q1 = s1[j];
-                const float dx = __fsub_rn(q0.x, fx);
+                const PowerX pxs = power_x(q0, __fsub_rn(q0.x, fx));
                 n_eval += active;
 #pragma unroll
                 for (int p = 0; p < PPT; p++) {
                     if (done[p]) continue;
-                    const float dy = __fsub_rn(q0.y, fy[p]);
-                    const float power = staged_power(q0, q1.x, dx, dy);
+                    const float power = power_at(pxs, q1.x, __fsub_rn(q0.y, fy[p]));
                     if (power > 0.f || power < q1.w) continue;
                     const float alpha = fminf(kAlphaMax, __fmul_rn(q1.y, __expf(power)));
                     const float testT = __fmul_rn(T[p], __fsub_rn(1.f, alpha));
