@@ -14,6 +14,7 @@ namespace cgs {
 
 constexpr int kGB = 64;          // Gaussians per block
 constexpr int kPreThreads = 256;
+constexpr int kPreBwdMinBlocks = 2;   // resident blocks per SM the backward is compiled for
 constexpr int kCamF = 23;        // staged camera: 20 ABI floats + camera centre
 
 // Real SH normalisation constants (closed forms: sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) x
@@ -432,7 +433,7 @@ __device__ __forceinline__ void project_bwd(const Staged &st, int gl, const floa
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(kPreThreads)
+__global__ void __launch_bounds__(kPreThreads, kPreBwdMinBlocks)
 k_preprocess_bwd(const float *__restrict__ P, int64_t n, const cgs_camera *__restrict__ cams, int V,
                  Grid grid, float near_z, const float4 *__restrict__ rec, const float4 *__restrict__ sgrad,
                  float *__restrict__ pgrad, int accumulate, float *__restrict__ accum,

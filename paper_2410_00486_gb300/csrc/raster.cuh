@@ -117,6 +117,17 @@ __host__ __device__ constexpr int ppt_for()
     return (B * B / P >= 32) ? P : (B * B / 32);
 }
 
+// Resident warps per SM each raster kernel is compiled for (__launch_bounds__ minimum
+// blocks): the register budget is 64K / (warps x 32).  The backward is latency-bound and
+// gains from more resident warps than its natural 80 registers allow.
+constexpr int kFwdMinWarps = 32;
+constexpr int kBwdMinWarps = 36;
+template <int B, int P, int MinWarps>
+__host__ __device__ constexpr int min_blocks_for()
+{
+    return MinWarps / (B * B / ppt_for<B, P>() / 32) > 0 ? MinWarps / (B * B / ppt_for<B, P>() / 32) : 1;
+}
+
 // Staged splat, derived exactly from its record (negation and scaling by 1/2 are exact):
 //   s0 = (u, v, -A/2, -B), s1 = (-C/2, opacity, depth, tau), s2 = (r, g, b, -)
 // where tau = -ln(255 opacity): alpha = opacity exp(power) < 1/255 exactly when

@@ -61,7 +61,7 @@ __device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane)
 }
 
 template <int B, int BD>
-__global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>()) k_render_bwd(RasterBwdArgs a)
+__global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<B, kPPTBwd, kBwdMinWarps>())) k_render_bwd(RasterBwdArgs a)
 {
     constexpr int PPT = ppt_for<B, kPPTBwd>();
     constexpr int NT = B * B / PPT;
@@ -84,13 +84,13 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>()) k_render_bwd(Ras
     // per-pixel state: transmittance, pixel gradients, and S = (colour behind) . gI +
     // (depth behind) gD, where "behind" starts as the background (no depth) and follows
     // R <- alpha c + (1 - alpha) R towards the front
-    float fy[PPT], T[PPT], gI0[PPT], gI1[PPT], gI2[PPT], gD[PPT], S[PPT];
+    float T[PPT], gI0[PPT], gI1[PPT], gI2[PPT], gD[PPT], S[PPT];
+    const float fy0 = (float)py0;   // row of pixel p: fy0 + p (exact)
     uint32_t lst[PPT];
     uint32_t m = 0;
 #pragma unroll
     for (int p = 0; p < PPT; p++) {
         const int py = py0 + p;
-        fy[p] = (float)py;
         lst[p] = 0;
         T[p] = 1.f;
         gI0[p] = gI1[p] = gI2[p] = gD[p] = S[p] = 0.f;
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>()) k_render_bwd(Ras
 #pragma unroll
             for (int p = 0; p < PPT; p++) {
                 if (!(pos < lst[p])) continue;
-                const float dy = __fsub_rn(q0.y, fy[p]);
+                const float dy = __fsub_rn(q0.y, fy0 + (float)p);
                 const float power = power_at(pxs, q1.x, dy);
                 if (power > 0.f || power < q1.w) continue;
                 const float G = __expf(power);

@@ -13,7 +13,7 @@
 namespace cgs {
 
 template <int B, int BD, bool CKPT>
-__global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>()) k_render_fwd(RasterFwdArgs a)
+__global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<B, kPPTFwd, kFwdMinWarps>())) k_render_fwd(RasterFwdArgs a)
 {
     constexpr int PPT = ppt_for<B, kPPTFwd>();
     constexpr int NT = B * B / PPT;
