@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", type=int, default=5)
     ap.add_argument("--tile", type=int, default=16)
-    ap.add_argument("--batch-depth", type=int, default=64)
+    ap.add_argument("--batch-depth", type=int, default=128, help="splats per staged batch, forward")
+    ap.add_argument("--batch-depth-bwd", type=int, default=64, help="splats per staged batch, backward")
     ap.add_argument("--autotune", action="store_true", help="pick tile/batch depth by measurement first")
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -256,14 +257,15 @@ def main():
     tgt_rgb, tgt_d = tgt_win.img.clone(), tgt_win.depth.clone()
     del tgt_win
 
-    tile, bd = args.tile, args.batch_depth
+    tile, bd, bdb = args.tile, args.batch_depth, args.batch_depth_bwd
     tuned = None
     if args.autotune:
         from paper_2410_00486_gb300.autotune import autotune
-        (tile, bd), res = autotune(params_t, n, sc.sh_degree, W, H, cams, tgt_rgb, tgt_d, log=log)
-        tuned = {f"{t}x{b}": round(ms, 3) for (t, b), ms in res.items()}
+        (tile, bd, bdb), res = autotune(params_t, n, sc.sh_degree, W, H, cams, tgt_rgb, tgt_d, log=log)
+        tuned = {"x".join(map(str, c)): round(ms, 3) for c, ms in res.items()}
 
-    win = MappingWindow(params_t.clone(), n, sc.sh_degree, W, H, V, tile=tile, batch_depth=bd)
+    win = MappingWindow(params_t.clone(), n, sc.sh_degree, W, H, V, tile=tile, batch_depth=bd,
+                        batch_depth_bwd=bdb)
     win.set_window(cams, tgt_rgb, tgt_d)
     ninst = win.fit_capacity(1.25)
     win.capture()
@@ -308,7 +310,7 @@ def main():
     per_view = None
     if not args.no_per_view:
         pv = MappingWindow(params_t.clone(), n, sc.sh_degree, W, H, V, tile=tile, batch_depth=bd,
-                           capacity=win.capacity)
+                           batch_depth_bwd=bdb, capacity=win.capacity)
         pv.set_window(cams, tgt_rgb, tgt_d)
         pv.step_per_view()
         torch.cuda.synchronize()
@@ -344,7 +346,7 @@ def main():
     # --- the same iteration with the SSIM term of Eq. 9 in the loss
     ssim = None
     if not args.no_ssim:
-        ssim = ssim_variant(MappingWindow, params_t, sc, tile, bd, cams, tgt_rgb, tgt_d, win.capacity,
+        ssim = ssim_variant(MappingWindow, params_t, sc, tile, (bd, bdb), cams, tgt_rgb, tgt_d, win.capacity,
                             max(3, args.steps // 4), args.warmup, args.lambda_ssim)
 
     # --- stage breakdown (eager, CUDA events on the launching stream)
@@ -374,7 +376,7 @@ def main():
         cpu = cpu_baseline(sc)
 
     if rank == 0:
-        extra = {"tile": tile, "batch_depth": bd, "tile_instances": ninst}
+        extra = {"tile": tile, "batch_depth": bd, "batch_depth_bwd": bdb, "tile_instances": ninst}
         if tuned:
             extra["autotune_ms"] = tuned
         line = {
@@ -451,7 +453,7 @@ def ssim_variant(MappingWindow, params_t, sc, tile, bd, cams, tgt_rgb, tgt_d, ca
     import torch
     from paper_2410_00486_gb300 import _native as N
     w = MappingWindow(params_t.clone(), sc.n, sc.sh_degree, sc.width, sc.height, sc.views, tile=tile,
-                      batch_depth=bd, capacity=capacity, lambda_ssim=lam)
+                      batch_depth=bd[0], batch_depth_bwd=bd[1], capacity=capacity, lambda_ssim=lam)
     w.set_window(cams, tgt_rgb, tgt_d)
     w.capture()
     for _ in range(warmup):

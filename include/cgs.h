@@ -81,6 +81,8 @@ typedef struct {
     float near_z;            /* near-plane cull: camera z must exceed this (0.2) */
     float bg[3];             /* background colour added with the final transmittance */
     float lambda_depth;      /* weight of the masked depth L1 term (0.1) */
+    int32_t batch_depth_bwd; /* splats per batch in the pixel-wise raster backward: 0 (same as
+                                batch_depth), 32, 64, 128 or 256 */
 } cgs_config;
 
 /* Number of floats in the parameter vector: (14 + 3 (K-1)) n. */

@@ -1,7 +1,10 @@
-"""Autotuner for the raster launch shape: tile edge B (8/16/32) and batch depth (splats
-staged per shared-memory batch).  Each candidate runs the whole captured window
-iteration on the caller's scene; the fastest (CUDA-event time) wins.  Results are
-cached per workload shape in memory and, when `cache_path` is given, in a JSON file.
+"""Autotuner for the raster launch shape: tile edge B (8/16/32) and the batch depths
+(splats staged per shared-memory batch) of the forward and of the backward.  Each
+candidate runs the whole captured window iteration on the caller's scene; the fastest
+(CUDA-event time) wins.  First every (tile, depth) pair with one depth for both kernels,
+then, at the best tile, each kernel's depth on its own (the two kernels are separate
+launches, so their best depths are independent).  Results are cached per workload shape
+in memory and, when `cache_path` is given, in a JSON file.
 """
 from __future__ import annotations
 
@@ -37,7 +40,7 @@ def time_window(win: MappingWindow, reps: int = 5, warmup: int = 2) -> float:
 
 def autotune(params: torch.Tensor, n: int, sh_degree: int, width: int, height: int, cams, tgt_rgb, tgt_depth,
              candidates=CANDIDATES, reps: int = 5, cache_path: str | Path | None = None, log=None, **kw):
-    """Return ((tile, batch_depth), {candidate: ms}) for this workload."""
+    """Return ((tile, batch_depth, batch_depth_bwd), {candidate: ms}) for this workload."""
     views = int(cams.shape[0])
     key = shape_key(n, sh_degree, width, height, views)
     if cache_path and Path(cache_path).exists():
@@ -47,20 +50,34 @@ def autotune(params: torch.Tensor, n: int, sh_degree: int, width: int, height: i
     if key in _memo:
         return _memo[key]
     results = {}
-    for tile, bd in candidates:
-        win = MappingWindow(params.clone(), n, sh_degree, width, height, views, tile=tile, batch_depth=bd, **kw)
+
+    def measure(tile, bd, bdb):
+        if (tile, bd, bdb) in results:
+            return
+        win = MappingWindow(params.clone(), n, sh_degree, width, height, views, tile=tile, batch_depth=bd,
+                            batch_depth_bwd=bdb, **kw)
         win.set_window(cams, tgt_rgb, tgt_depth)
         win.fit_capacity(1.3)
-        results[(tile, bd)] = time_window(win, reps)
+        results[(tile, bd, bdb)] = time_window(win, reps)
         if log:
-            log(f"autotune tile={tile} batch_depth={bd}: {results[(tile, bd)]:.3f} ms")
+            log(f"autotune tile={tile} batch_depth={bd} batch_depth_bwd={bdb}: {results[(tile, bd, bdb)]:.3f} ms")
         del win
         torch.cuda.empty_cache()
+
+    for tile, bd in candidates:
+        measure(tile, bd, bd)
+    tile, bd, bdb = min(results, key=results.get)
+    depths = sorted({b for _, b in candidates})
+    for d in depths:                       # forward depth, backward depth held
+        measure(tile, d, bdb)
+    bd = min((d for d in depths), key=lambda d: results[(tile, d, bdb)])
+    for d in depths:                       # backward depth, forward depth held
+        measure(tile, bd, d)
     best = min(results, key=results.get)
     _memo[key] = (best, results)
     if cache_path:
         p = Path(cache_path)
         disk = json.loads(p.read_text()) if p.exists() else {}
-        disk[key] = {"best": list(best), "ms": {f"{t}x{b}": v for (t, b), v in results.items()}}
+        disk[key] = {"best": list(best), "ms": {"x".join(map(str, c)): v for c, v in results.items()}}
         p.write_text(json.dumps(disk, indent=1))
     return best, results

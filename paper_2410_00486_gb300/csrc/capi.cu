@@ -37,6 +37,9 @@ bool cfg_ok(const cgs_config *c)
     if (c->width < 1 || c->height < 1 || c->width > (1 << 16) || c->height > (1 << 16)) return false;
     if (c->tile != 8 && c->tile != 16 && c->tile != 32) return false;
     if (c->batch_depth != 32 && c->batch_depth != 64 && c->batch_depth != 128 && c->batch_depth != 256) return false;
+    if (c->batch_depth_bwd != 0 && c->batch_depth_bwd != 32 && c->batch_depth_bwd != 64 &&
+        c->batch_depth_bwd != 128 && c->batch_depth_bwd != 256)
+        return false;
     if (c->sh_degree < 0 || c->sh_degree > 3) return false;
     if (!(c->near_z > 0.f) || !isfinite(c->near_z)) return false;
     return true;
@@ -201,7 +204,8 @@ int cgs_raster_bwd(const float *rec, const uint32_t *vals, const uint32_t *range
     a.dl_dimg = dl_dimg;
     a.dl_ddepth = dl_ddepth;
     a.sgrad = slot_grad;
-    return cuda_status(raster_bwd(a, cfg->tile, cfg->batch_depth, (cudaStream_t)stream));
+    const int bd = cfg->batch_depth_bwd ? cfg->batch_depth_bwd : cfg->batch_depth;
+    return cuda_status(raster_bwd(a, cfg->tile, bd, (cudaStream_t)stream));
 }
 
 int cgs_preprocess_bwd(const float *params, int64_t n, const cgs_camera *cams, int32_t V, const cgs_config *cfg,

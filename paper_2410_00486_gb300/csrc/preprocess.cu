@@ -15,6 +15,7 @@ namespace cgs {
 constexpr int kGB = 64;          // Gaussians per block
 constexpr int kPreThreads = 256;
 constexpr int kPreBwdMinBlocks = 2;   // resident blocks per SM the backward is compiled for
+constexpr int kViewChunk = 64;        // views per compaction round of the backward
 constexpr int kCamF = 23;        // staged camera: 20 ABI floats + camera centre
 
 // Real SH normalisation constants (closed forms: sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) x
@@ -447,29 +448,57 @@ k_preprocess_bwd(const float *__restrict__ P, int64_t n, const cgs_camera *__res
     float *acc = sm;                    // gradient accumulators, staged layout
     float *dstat = sm + NS;             // densify stats: accum, denom, max radius (3 x kGB)
     for (int i = threadIdx.x; i < NS + 3 * kGB; i += blockDim.x) acc[i] = 0.f;
+    // visible (view, Gaussian) items of the block, compacted (per chunk of kViewChunk views)
+    // so that the chain rule runs with full warps: most slots of a view are culled
+    uint16_t *items = reinterpret_cast<uint16_t *>(sm + 2 * NS + 3 * kGB + V * kCamF);
+    __shared__ int wcount[kPreThreads / 32];
     Staged st = stage<DEG>(sm + NS + 3 * kGB, P, n, g0, cnt, cams, V);
     const bool stats = accum != nullptr;
-    for (int it = threadIdx.x; it < kGB * V; it += blockDim.x) {
-        const int gl = it % kGB, v = it / kGB;
-        if (gl >= cnt) continue;
-        const int64_t slot = (int64_t)v * n + g0 + gl;
-        const float4 *r = rec + kRec4 * slot;
-        const int rad = __float_as_int(__ldg(reinterpret_cast<const float *>(r) + 7));
-        if (rad <= 0) continue;
-        const float4 *gp = sgrad + kRec4 * slot;
-        float4 G0 = gp[0], G1 = gp[1], G2 = gp[2];
-        Proj<DEG> o;
-        project<DEG>(st, gl, st.cams + v * kCamF, grid, near_z, o);
-        if (!o.visible) continue;   // cannot happen for a slot the forward marked visible
-        project_bwd<DEG>(st, gl, st.cams + v * kCamF, o, G0, G1, G2, acc);
-        if (stats) {
-            float gx = G0.x * 0.5f * (float)grid.W, gy = G0.y * 0.5f * (float)grid.H;
-            atomicAdd(&dstat[gl], sqrtf(gx * gx + gy * gy));
-            atomicAdd(&dstat[kGB + gl], 1.0f);
-            atomicMax(reinterpret_cast<int *>(&dstat[2 * kGB + gl]), __float_as_int((float)rad));
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int v0 = 0; v0 < V; v0 += kViewChunk) {
+        const int nit = kGB * min(kViewChunk, V - v0);
+        int nitems = 0;
+        for (int c0 = 0; c0 < nit; c0 += kPreThreads) {
+            const int it = c0 + (int)threadIdx.x;
+            const int gl = it % kGB, v = v0 + it / kGB;
+            bool vis = false;
+            if (it < nit && gl < cnt) {
+                const float *r = reinterpret_cast<const float *>(rec + kRec4 * ((int64_t)v * n + g0 + gl));
+                vis = __float_as_int(__ldg(r + 7)) > 0;
+            }
+            const unsigned b = __ballot_sync(kFull, vis);
+            if (lane == 0) wcount[wp] = __popc(b);
+            __syncthreads();
+            int off = nitems, tot = 0;
+            for (int i = 0; i < kPreThreads / 32; i++) {
+                off += i < wp ? wcount[i] : 0;
+                tot += wcount[i];
+            }
+            if (vis) items[off + __popc(b & ((1u << lane) - 1u))] = (uint16_t)it;
+            nitems += tot;
+            __syncthreads();
         }
+        for (int k = threadIdx.x; k < nitems; k += blockDim.x) {
+            const int it = items[k];
+            const int gl = it % kGB, v = v0 + it / kGB;
+            const int64_t slot = (int64_t)v * n + g0 + gl;
+            const float4 *r = rec + kRec4 * slot;
+            const int rad = __float_as_int(__ldg(reinterpret_cast<const float *>(r) + 7));
+            const float4 *gp = sgrad + kRec4 * slot;
+            float4 G0 = gp[0], G1 = gp[1], G2 = gp[2];
+            Proj<DEG> o;
+            project<DEG>(st, gl, st.cams + v * kCamF, grid, near_z, o);
+            if (!o.visible) continue;   // cannot happen for a slot the forward marked visible
+            project_bwd<DEG>(st, gl, st.cams + v * kCamF, o, G0, G1, G2, acc);
+            if (stats) {
+                float gx = G0.x * 0.5f * (float)grid.W, gy = G0.y * 0.5f * (float)grid.H;
+                atomicAdd(&dstat[gl], sqrtf(gx * gx + gy * gy));
+                atomicAdd(&dstat[kGB + gl], 1.0f);
+                atomicMax(reinterpret_cast<int *>(&dstat[2 * kGB + gl]), __float_as_int((float)rad));
+            }
+        }
+        __syncthreads();   // the item list is rebuilt for the next chunk of views
     }
-    __syncthreads();
     // write the block's slice of every group (coalesced)
     const Layout L = param_layout(n, DEG);
     const int widths[6] = {3, 3, 4, 1, 3, 3 * (K - 1)};
@@ -516,7 +545,8 @@ static cudaError_t launch_pre_bwd(const float *P, int64_t n, const cgs_camera *c
                                   float near_z, const float4 *rec, const float4 *sgrad, float *pgrad,
                                   int accumulate, float *accum, float *denom, float *maxr, cudaStream_t s)
 {
-    size_t smem = sizeof(float) * (2 * (size_t)staged_floats<DEG>() + 3 * kGB + (size_t)V * kCamF);
+    size_t smem = sizeof(float) * (2 * (size_t)staged_floats<DEG>() + 3 * kGB + (size_t)V * kCamF) +
+                  sizeof(uint16_t) * (size_t)kGB * kViewChunk;
     auto k = k_preprocess_bwd<DEG>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

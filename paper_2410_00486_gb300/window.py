@@ -40,14 +40,15 @@ class MappingWindow:
                  lambda_depth: float = 0.1, bg=(0.0, 0.0, 0.0), near_z: float = 0.2,
                  betas=(0.9, 0.999), eps: float = 1e-15, capacity: int | None = None,
                  densify_stats: bool = True, tile_order: bool = True, backward: str = "pixel",
-                 lambda_ssim: float = 0.0):
+                 lambda_ssim: float = 0.0, batch_depth_bwd: int = 0):
         if not params.is_cuda or params.dtype != torch.float32:
             raise ValueError("params must be a float32 CUDA tensor")
         dev = params.device
         self.device = dev
         self.n, self.V, self.sh_degree = int(n), int(views), int(sh_degree)
         self.W, self.H = int(width), int(height)
-        self.cfg = N.make_config(width, height, tile, batch_depth, sh_degree, near_z, bg, lambda_depth)
+        self.cfg = N.make_config(width, height, tile, batch_depth, sh_degree, near_z, bg, lambda_depth,
+                                 batch_depth_bwd)
         P = N.cgs_param_count(n, sh_degree)
         if params.numel() != P:
             raise ValueError(f"params has {params.numel()} floats, expected {P}")

@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(native):
 
 def test_struct_sizes_match_header(native):
     assert ctypes.sizeof(native.cgs_camera) == 80
-    assert ctypes.sizeof(native.cgs_config) == 4 * 10
+    assert ctypes.sizeof(native.cgs_config) == 4 * 11
 
 
 def test_host_only_queries(native):
@@ -55,6 +55,8 @@ def test_argument_validation_needs_no_gpu(native):
     # null pointers / bad sizes / bad options are refused before any CUDA call
     assert L.cgs_preprocess(None, 10, None, 1, ctypes.byref(cfg), None, None, None, None) == native.CGS_ERR_ARG
     bad = native.make_config(64, 48, 16, 48, 1)
+    assert L.cgs_preprocess(8, 10, 16, 1, ctypes.byref(bad), 16, None, None, None) == native.CGS_ERR_ARG
+    bad = native.make_config(64, 48, 16, 64, 1, batch_depth_bwd=48)
     assert L.cgs_preprocess(8, 10, 16, 1, ctypes.byref(bad), 16, None, None, None) == native.CGS_ERR_ARG
     assert L.cgs_preprocess(8, 0, 16, 1, ctypes.byref(cfg), 16, None, None, None) == native.CGS_ERR_ARG
     assert L.cgs_preprocess(8, 10, 16, 1, ctypes.byref(cfg), 8, None, None, None) == native.CGS_ERR_ARG  # unaligned
