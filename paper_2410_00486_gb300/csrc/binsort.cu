@@ -92,6 +92,58 @@ __global__ void k_count(const float4 *__restrict__ rec, int64_t n, int V, Grid g
 constexpr int kChunk = 4096;
 constexpr int kAggThreads = 512;
 
+// Calls f(ty, x0, x1, key) for every tile row [x0, x1) x {ty} of the rectangles of the
+// visible slots [s0, s1) of a view, load-balanced over the lanes of each warp: a warp
+// takes 32 slots, forms the prefix sum of their row counts, and hands out rows
+// round-robin; a lane finds the slot owning row j by a 5-step binary search over the
+// prefix (shuffles).  Slot order within a warp is kept, so a warp's calls for one tile
+// come in slot order within each round.
+template <class F>
+__device__ __forceinline__ void for_each_tile_row(const float4 *__restrict__ rec, int64_t n, int view, int64_t s0,
+                                                  int64_t s1, const Grid &g, F f)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t wb = s0 + (int64_t)(threadIdx.x & ~31u); wb < s1; wb += blockDim.x) {   // warp-uniform
+        const int64_t gi = wb + lane;
+        int h = 0, x0 = 0, x1 = 0, y0 = 0;
+        uint32_t zb = 0;
+        float u, v, z;
+        int r;
+        if (gi < s1 && load_slot(rec, (int64_t)view * n + gi, u, v, z, r)) {
+            const Rect R = tile_rect(u, v, r, g);
+            if (R.x1 > R.x0 && R.y1 > R.y0) {
+                h = R.y1 - R.y0;
+                x0 = R.x0;
+                x1 = R.x1;
+                y0 = R.y0;
+                zb = __float_as_uint(z);
+            }
+        }
+        int incl = h;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, off);
+            if (lane >= off) incl += y;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        for (int r0 = 0; r0 < total; r0 += 32) {
+            const int j = r0 + lane;
+            int L = 0;   // owner: the number of lanes whose inclusive prefix is <= j
+#pragma unroll
+            for (int b = 16; b > 0; b >>= 1)
+                if (__shfl_sync(kFull, incl, L + b - 1) <= j) L += b;
+            const int oend = __shfl_sync(kFull, incl, L), oh = __shfl_sync(kFull, h, L);
+            const int ox0 = __shfl_sync(kFull, x0, L), ox1 = __shfl_sync(kFull, x1, L);
+            const int oy0 = __shfl_sync(kFull, y0, L);
+            const uint32_t ozb = __shfl_sync(kFull, zb, L);
+            if (j < total) {
+                const uint32_t slot = (uint32_t)((int64_t)view * n + wb + L);
+                f(oy0 + (j - (oend - oh)), ox0, ox1, ((uint64_t)ozb << 32) | (uint64_t)slot);
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kAggThreads)
 k_count_agg(const float4 *__restrict__ rec, int64_t n, Grid g, uint32_t *__restrict__ count)
 {
@@ -101,14 +153,9 @@ k_count_agg(const float4 *__restrict__ rec, int64_t n, Grid g, uint32_t *__restr
     const int64_t s1 = min(n, s0 + kChunk);
     for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) hist[t] = 0;
     __syncthreads();
-    for (int64_t gi = s0 + threadIdx.x; gi < s1; gi += blockDim.x) {
-        float u, v, z;
-        int r;
-        if (!load_slot(rec, (int64_t)view * n + gi, u, v, z, r)) continue;
-        Rect R = tile_rect(u, v, r, g);
-        for (int ty = R.y0; ty < R.y1; ty++)
-            for (int tx = R.x0; tx < R.x1; tx++) atomicAdd(&hist[ty * g.Tx + tx], 1u);
-    }
+    for_each_tile_row(rec, n, view, s0, s1, g, [&](int ty, int x0, int x1, uint64_t) {
+        for (int tx = x0; tx < x1; tx++) atomicAdd(&hist[ty * g.Tx + tx], 1u);
+    });
     __syncthreads();
     uint32_t *base = count + (int64_t)view * g.Tv;
     for (int t = threadIdx.x; t < g.Tv; t += blockDim.x)
@@ -202,14 +249,9 @@ k_scatter_agg(const float4 *__restrict__ rec, int64_t n, Grid g, const uint32_t 
     const int64_t s1 = min(n, s0 + kChunk);
     for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) hist[t] = 0;
     __syncthreads();
-    for (int64_t gi = s0 + threadIdx.x; gi < s1; gi += blockDim.x) {
-        float u, v, z;
-        int r;
-        if (!load_slot(rec, (int64_t)view * n + gi, u, v, z, r)) continue;
-        Rect R = tile_rect(u, v, r, g);
-        for (int ty = R.y0; ty < R.y1; ty++)
-            for (int tx = R.x0; tx < R.x1; tx++) atomicAdd(&hist[ty * g.Tx + tx], 1u);
-    }
+    for_each_tile_row(rec, n, view, s0, s1, g, [&](int ty, int x0, int x1, uint64_t) {
+        for (int tx = x0; tx < x1; tx++) atomicAdd(&hist[ty * g.Tx + tx], 1u);
+    });
     __syncthreads();
     const int64_t tbase = (int64_t)view * g.Tv;
     for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) {
@@ -217,19 +259,12 @@ k_scatter_agg(const float4 *__restrict__ rec, int64_t n, Grid g, const uint32_t 
         if (c) hist[t] = start[tbase + t] + atomicAdd(cursor + tbase + t, c);
     }
     __syncthreads();
-    for (int64_t gi = s0 + threadIdx.x; gi < s1; gi += blockDim.x) {
-        const int64_t s = (int64_t)view * n + gi;
-        float u, v, z;
-        int r;
-        if (!load_slot(rec, s, u, v, z, r)) continue;
-        Rect R = tile_rect(u, v, r, g);
-        const uint64_t key = ((uint64_t)__float_as_uint(z) << 32) | (uint64_t)(uint32_t)s;
-        for (int ty = R.y0; ty < R.y1; ty++)
-            for (int tx = R.x0; tx < R.x1; tx++) {
-                const uint64_t pos = atomicAdd(&hist[ty * g.Tx + tx], 1u);
-                if (pos < (uint64_t)capacity) keys[pos] = key;
-            }
-    }
+    for_each_tile_row(rec, n, view, s0, s1, g, [&](int ty, int x0, int x1, uint64_t key) {
+        for (int tx = x0; tx < x1; tx++) {
+            const uint64_t pos = atomicAdd(&hist[ty * g.Tx + tx], 1u);
+            if (pos < (uint64_t)capacity) keys[pos] = key;
+        }
+    });
 }
 
 // Compare-exchange network of an ascending bitonic sort in which every comparator
