@@ -666,8 +666,9 @@ def roofline(stages, work, clocks):
 def end_to_end(win, sc, cams, tgt_rgb, tgt_d, args, torch, N):
     """Steps through the public API: the adaptive scheduler (Eqs. 5-8) draws the window's
     view weights, the window's cameras, targets and weights are copied from pinned host
-    memory, the captured iteration runs, and the per-view losses are read back and
-    reported to the scheduler."""
+    memory (cameras and targets staged on a copy stream during the previous iteration),
+    the captured iteration runs, and the per-view losses are read back and reported to the
+    scheduler.  Every step copies the whole window's inputs."""
     from paper_2410_00486_gb300 import Scheduler
     V = sc.views
     h_cams = cams.cpu().pin_memory()
@@ -680,19 +681,27 @@ def end_to_end(win, sc, cams, tgt_rgb, tgt_d, args, torch, N):
         sched.add(v, 8)
     rng = np.random.default_rng(0)
 
+    done = torch.cuda.Event()
+
     def one_step():
+        # the draws need the previous window's losses (reported below); the next window's
+        # cameras and targets do not, so their copy is staged while this iteration runs
         counts = np.zeros(V, np.float32)
         for _ in range(V):
             counts[sched.draw(int(rng.integers(0, 2 ** 32)))] += 1.0
         h_w.copy_(torch.from_numpy(counts))
-        win.set_window(h_cams, h_rgb, h_d, h_w, non_blocking=True)
+        win.set_view_weight(h_w)
+        win.commit_window()
         win.replay()
         h_loss.copy_(win.loss_view, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        done.record()
+        win.stage_window(h_cams, h_rgb, h_d)
+        done.synchronize()
         for v in range(V):
             if counts[v] > 0:
                 sched.report(v, float(h_loss[v]) / counts[v])
 
+    win.stage_window(h_cams, h_rgb, h_d)
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
@@ -700,6 +709,7 @@ def end_to_end(win, sc, cams, tgt_rgb, tgt_d, args, torch, N):
     steps = max(3, args.steps // 4)
     for _ in range(steps):
         one_step()
+    torch.cuda.synchronize()
     sec = time.perf_counter() - t0
     h2d = h_cams.numel() * 4 + h_rgb.numel() * 4 + h_d.numel() * 4 + h_w.numel() * 4
     return {"value": steps / sec, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": V * 4,

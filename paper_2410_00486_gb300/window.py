@@ -137,6 +137,43 @@ class MappingWindow:
         if view_weight is not None:
             self.view_weight.copy_(torch.as_tensor(view_weight, dtype=torch.float32), non_blocking=non_blocking)
 
+    def set_view_weight(self, view_weight, non_blocking=True):
+        self.view_weight.copy_(torch.as_tensor(view_weight, dtype=torch.float32), non_blocking=non_blocking)
+
+    # ------------------------------------------------- pipelined input copies
+    def stage_window(self, cams, tgt_rgb, tgt_depth=None):
+        """Start copying the next window's cameras and targets from (pinned) host memory into
+        device staging buffers on the window's copy stream, so the copy overlaps an iteration
+        still running on the compute stream.  `commit_window()` makes them current."""
+        if not hasattr(self, "_stage"):
+            self._copy_stream = torch.cuda.Stream(device=self.device)
+            self._stage = (torch.empty_like(self.cams), torch.empty_like(self.tgt_rgb),
+                           torch.empty_like(self.tgt_depth))
+            self._staged = torch.cuda.Event()
+            self._consumed = torch.cuda.Event()
+            self._consumed.record(torch.cuda.current_stream(self.device))
+        c, r, d = self._stage
+        with torch.cuda.stream(self._copy_stream):
+            self._copy_stream.wait_event(self._consumed)       # the previous staging was committed
+            c.copy_(torch.as_tensor(cams).reshape(c.shape), non_blocking=True)
+            r.copy_(torch.as_tensor(tgt_rgb).reshape(r.shape), non_blocking=True)
+            if tgt_depth is not None:
+                d.copy_(torch.as_tensor(tgt_depth).reshape(d.shape), non_blocking=True)
+            else:
+                d.zero_()
+            self._staged.record(self._copy_stream)
+
+    def commit_window(self):
+        """Make the staged inputs current: the compute stream waits for the staging copy, then
+        copies device to device into the buffers the iteration (and a captured graph) reads."""
+        cur = torch.cuda.current_stream(self.device)
+        cur.wait_event(self._staged)
+        c, r, d = self._stage
+        self.cams.copy_(c)
+        self.tgt_rgb.copy_(r)
+        self.tgt_depth.copy_(d)
+        self._consumed.record(cur)
+
     # ---------------------------------------------------------- iteration
     def forward(self, with_loss: bool = True, params: torch.Tensor | None = None):
         """Preprocess, bin and render every view of the window (loss fused if with_loss;

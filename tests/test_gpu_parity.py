@@ -917,3 +917,33 @@ def test_window_add_points_then_iterate():
     torch.cuda.synchronize()
     assert win.read_status()[0] == 0
     assert torch.isfinite(win.params).all()
+
+
+def test_staged_window_inputs_equal_direct_copy():
+    """Cameras and targets staged on the copy stream during an iteration, then committed,
+    give the same iteration as a direct copy."""
+    torch = torch_cuda()
+    native()
+    from paper_2410_00486_gb300.window import MappingWindow
+    sc, tgt_rgb, tgt_d = scene("path_sh3_3views")
+    params, cams = gpu_scene_tensors(sc)
+    h_cams, h_rgb, h_d = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                          for a in (sc.cams, tgt_rgb, tgt_d))
+    a = MappingWindow(params.clone(), sc.n, 3, sc.width, sc.height, sc.views, tile=16)
+    b = MappingWindow(params.clone(), sc.n, 3, sc.width, sc.height, sc.views, tile=16)
+    a.set_window(h_cams, h_rgb, h_d)
+    b.set_window(h_cams, torch.zeros_like(h_rgb), None)      # stale inputs, replaced below
+    for w in (a, b):
+        w.fit_capacity(2.0)
+    b.capture()
+    b.stage_window(h_cams, h_rgb, h_d)
+    b.forward()                                              # renders the stale inputs meanwhile
+    b.commit_window()
+    b.replay()
+    a.step()
+    torch.cuda.synchronize()
+    assert torch.equal(a.tgt_rgb, b.tgt_rgb) and torch.equal(a.tgt_depth, b.tgt_depth)
+    assert torch.equal(a.img, b.img)
+    torch.testing.assert_close(b.loss_view, a.loss_view, rtol=1e-5, atol=0)
+    d = (a.params - b.params).abs()
+    assert (d > 1e-5).float().mean().item() < 1e-3
