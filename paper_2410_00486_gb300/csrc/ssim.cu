@@ -21,6 +21,7 @@ constexpr int kSsimR = 5;                    // window radius
 constexpr int kSsimT = 32;                   // output tile edge
 constexpr int kSsimIn = kSsimT + 2 * kSsimR;  // staged edge
 constexpr float kC1 = 0.0001f, kC2 = 0.0009f;
+constexpr int kRB = 4;                       // outputs per thread along a blur pass
 
 struct SsimTaps {
     float g[2 * kSsimR + 1];
@@ -47,52 +48,72 @@ k_ssim_fwd(const float *__restrict__ img, const float *__restrict__ tgt, int W, 
         sy[r][c] = in ? tgt[plane + (size_t)gy * W + gx] : 0.f;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kSsimIn * kSsimT; i += blockDim.x) {
-        const int r = i / kSsimT, c = i % kSsimT;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+    // horizontal pass, kRB adjacent outputs per thread from kRB + 10 staged values
+    for (int i = threadIdx.x; i < kSsimIn * (kSsimT / kRB); i += blockDim.x) {
+        const int r = i / (kSsimT / kRB), c0 = (i % (kSsimT / kRB)) * kRB;
+        float xs[kRB + 2 * kSsimR], ys[kRB + 2 * kSsimR];
 #pragma unroll
-        for (int k = 0; k < 2 * kSsimR + 1; k++) {
-            const float xv = sx[r][c + k], yv = sy[r][c + k], w = t.g[k];
-            a0 = fmaf(w, xv, a0);
-            a1 = fmaf(w, yv, a1);
-            a2 = fmaf(w, xv * xv, a2);
-            a3 = fmaf(w, yv * yv, a3);
-            a4 = fmaf(w, xv * yv, a4);
+        for (int k = 0; k < kRB + 2 * kSsimR; k++) {
+            xs[k] = sx[r][c0 + k];
+            ys[k] = sy[r][c0 + k];
         }
-        hm[0][r][c] = a0;
-        hm[1][r][c] = a1;
-        hm[2][r][c] = a2;
-        hm[3][r][c] = a3;
-        hm[4][r][c] = a4;
+#pragma unroll
+        for (int o = 0; o < kRB; o++) {
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 2 * kSsimR + 1; k++) {
+                const float xv = xs[o + k], yv = ys[o + k], w = t.g[k];
+                a0 = fmaf(w, xv, a0);
+                a1 = fmaf(w, yv, a1);
+                a2 = fmaf(w, xv * xv, a2);
+                a3 = fmaf(w, yv * yv, a3);
+                a4 = fmaf(w, xv * yv, a4);
+            }
+            hm[0][r][c0 + o] = a0;
+            hm[1][r][c0 + o] = a1;
+            hm[2][r][c0 + o] = a2;
+            hm[3][r][c0 + o] = a3;
+            hm[4][r][c0 + o] = a4;
+        }
     }
     __syncthreads();
     float sS = 0.f, sR = 0.f;
-    for (int i = threadIdx.x; i < kSsimT * kSsimT; i += blockDim.x) {
-        const int r = i / kSsimT, c = i % kSsimT;
-        const int gx = blockIdx.x * kSsimT + c, gy = blockIdx.y * kSsimT + r;
-        if (gx >= W || gy >= H) continue;
-        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+    // vertical pass: kRB rows of one column per thread (kSsimT x kSsimT / kRB = 256 items)
+    for (int i = threadIdx.x; i < kSsimT * (kSsimT / kRB); i += blockDim.x) {
+        const int c = i % kSsimT, r0 = (i / kSsimT) * kRB;
+        float mom[5][kRB];
 #pragma unroll
-        for (int k = 0; k < 2 * kSsimR + 1; k++) {
-            const float w = t.g[k];
-            mx = fmaf(w, hm[0][r + k][c], mx);
-            my = fmaf(w, hm[1][r + k][c], my);
-            exx = fmaf(w, hm[2][r + k][c], exx);
-            eyy = fmaf(w, hm[3][r + k][c], eyy);
-            exy = fmaf(w, hm[4][r + k][c], exy);
+        for (int m = 0; m < 5; m++) {
+            float col[kRB + 2 * kSsimR];
+#pragma unroll
+            for (int k = 0; k < kRB + 2 * kSsimR; k++) col[k] = hm[m][r0 + k][c];
+#pragma unroll
+            for (int o = 0; o < kRB; o++) {
+                float a = 0.f;
+#pragma unroll
+                for (int k = 0; k < 2 * kSsimR + 1; k++) a = fmaf(t.g[k], col[o + k], a);
+                mom[m][o] = a;
+            }
         }
-        const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-        const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
-        const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
-        const float inv = 1.f / (B1 * B2);
-        const float S = A1 * A2 * inv;
-        const float dA1 = A2 * inv, dA2 = A1 * inv, dB1 = -S / B1, dB2 = -S / B2;
-        const size_t q = plane + (size_t)gy * W + gx;
-        amap[q] = 2.f * my * (dA1 - dA2) + 2.f * mx * (dB1 - dB2);
-        bmap[q] = dB2;
-        cmap[q] = 2.f * dA2;
-        sS += S;
-        sR += fabsf(sx[r + kSsimR][c + kSsimR] - sy[r + kSsimR][c + kSsimR]);
+#pragma unroll
+        for (int o = 0; o < kRB; o++) {
+            const int r = r0 + o;
+            const int gx = blockIdx.x * kSsimT + c, gy = blockIdx.y * kSsimT + r;
+            if (gx >= W || gy >= H) continue;
+            const float mx = mom[0][o], my = mom[1][o];
+            const float sxx = mom[2][o] - mx * mx, syy = mom[3][o] - my * my, sxy = mom[4][o] - mx * my;
+            const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
+            const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
+            const float inv = 1.f / (B1 * B2);
+            const float S = A1 * A2 * inv;
+            const float dA1 = A2 * inv, dA2 = A1 * inv, dB1 = -S / B1, dB2 = -S / B2;
+            const size_t q = plane + (size_t)gy * W + gx;
+            amap[q] = 2.f * my * (dA1 - dA2) + 2.f * mx * (dB1 - dB2);
+            bmap[q] = dB2;
+            cmap[q] = 2.f * dA2;
+            sS += S;
+            sR += fabsf(sx[r + kSsimR][c + kSsimR] - sy[r + kSsimR][c + kSsimR]);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         sS += __shfl_xor_sync(kFull, sS, o);
@@ -138,53 +159,66 @@ k_ssim_bwd(const float *__restrict__ img, const float *__restrict__ tgt, const f
         sa[2][r][c] = in ? cmap[q] : 0.f;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kSsimIn * kSsimT; i += blockDim.x) {
-        const int r = i / kSsimT, c = i % kSsimT;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (int i = threadIdx.x; i < kSsimIn * (kSsimT / kRB); i += blockDim.x) {
+        const int r = i / (kSsimT / kRB), c0 = (i % (kSsimT / kRB)) * kRB;
 #pragma unroll
-        for (int k = 0; k < 2 * kSsimR + 1; k++) {
-            const float w = t.g[k];
-            a0 = fmaf(w, sa[0][r][c + k], a0);
-            a1 = fmaf(w, sa[1][r][c + k], a1);
-            a2 = fmaf(w, sa[2][r][c + k], a2);
+        for (int m = 0; m < 3; m++) {
+            float row[kRB + 2 * kSsimR];
+#pragma unroll
+            for (int k = 0; k < kRB + 2 * kSsimR; k++) row[k] = sa[m][r][c0 + k];
+#pragma unroll
+            for (int o = 0; o < kRB; o++) {
+                float a = 0.f;
+#pragma unroll
+                for (int k = 0; k < 2 * kSsimR + 1; k++) a = fmaf(t.g[k], row[o + k], a);
+                hb[m][r][c0 + o] = a;
+            }
         }
-        hb[0][r][c] = a0;
-        hb[1][r][c] = a1;
-        hb[2][r][c] = a2;
     }
     __syncthreads();
     const float M = 3.f * (float)W * (float)H;
     const float wv = weight ? weight[v] : 1.f;
     const int cnt = depth_count ? depth_count[v] : 0;
     float sD = 0.f;
-    for (int i = threadIdx.x; i < kSsimT * kSsimT; i += blockDim.x) {
-        const int r = i / kSsimT, c = i % kSsimT;
-        const int gx = blockIdx.x * kSsimT + c, gy = blockIdx.y * kSsimT + r;
-        if (gx >= W || gy >= H) continue;
-        float ba = 0.f, bb = 0.f, bc = 0.f;
+    for (int i = threadIdx.x; i < kSsimT * (kSsimT / kRB); i += blockDim.x) {
+        const int c = i % kSsimT, r0 = (i / kSsimT) * kRB;
+        float bl[3][kRB];
 #pragma unroll
-        for (int k = 0; k < 2 * kSsimR + 1; k++) {
-            const float w = t.g[k];
-            ba = fmaf(w, hb[0][r + k][c], ba);
-            bb = fmaf(w, hb[1][r + k][c], bb);
-            bc = fmaf(w, hb[2][r + k][c], bc);
-        }
-        const size_t q = plane + (size_t)gy * W + gx;
-        const float xv = img[q], yv = tgt[q];
-        const float sgn = xv > yv ? 1.f : (xv < yv ? -1.f : 0.f);
-        dl_dimg[q] = wv * ((1.f - lam) * sgn / M - lam / M * (ba + 2.f * xv * bb + yv * bc));
-        if (ch == 0 && dl_ddepth) {
-            const size_t pix = (size_t)v * W * H + (size_t)gy * W + gx;
-            float gd = 0.f;
-            if (tgt_depth && cnt > 0) {
-                const float td = tgt_depth[pix];
-                if (td > 0.f) {
-                    const float dd = depth[pix] - td;
-                    gd = wv * lambda_d * (dd > 0.f ? 1.f : (dd < 0.f ? -1.f : 0.f)) / (float)cnt;
-                    sD += fabsf(dd);
-                }
+        for (int m = 0; m < 3; m++) {
+            float col[kRB + 2 * kSsimR];
+#pragma unroll
+            for (int k = 0; k < kRB + 2 * kSsimR; k++) col[k] = hb[m][r0 + k][c];
+#pragma unroll
+            for (int o = 0; o < kRB; o++) {
+                float a = 0.f;
+#pragma unroll
+                for (int k = 0; k < 2 * kSsimR + 1; k++) a = fmaf(t.g[k], col[o + k], a);
+                bl[m][o] = a;
             }
-            dl_ddepth[pix] = gd;
+        }
+#pragma unroll
+        for (int o = 0; o < kRB; o++) {
+            const int r = r0 + o;
+            const int gx = blockIdx.x * kSsimT + c, gy = blockIdx.y * kSsimT + r;
+            if (gx >= W || gy >= H) continue;
+            const float ba = bl[0][o], bb = bl[1][o], bc = bl[2][o];
+            const size_t q = plane + (size_t)gy * W + gx;
+            const float xv = img[q], yv = tgt[q];
+            const float sgn = xv > yv ? 1.f : (xv < yv ? -1.f : 0.f);
+            dl_dimg[q] = wv * ((1.f - lam) * sgn / M - lam / M * (ba + 2.f * xv * bb + yv * bc));
+            if (ch == 0 && dl_ddepth) {
+                const size_t pix = (size_t)v * W * H + (size_t)gy * W + gx;
+                float gd = 0.f;
+                if (tgt_depth && cnt > 0) {
+                    const float td = tgt_depth[pix];
+                    if (td > 0.f) {
+                        const float dd = depth[pix] - td;
+                        gd = wv * lambda_d * (dd > 0.f ? 1.f : (dd < 0.f ? -1.f : 0.f)) / (float)cnt;
+                        sD += fabsf(dd);
+                    }
+                }
+                dl_ddepth[pix] = gd;
+            }
         }
     }
     if (ch == 0) {
