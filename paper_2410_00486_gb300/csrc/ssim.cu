@@ -34,8 +34,9 @@ __global__ void __launch_bounds__(256)
 k_ssim_fwd(const float *__restrict__ img, const float *__restrict__ tgt, int W, int H, SsimTaps t,
            float *__restrict__ amap, float *__restrict__ bmap, float *__restrict__ cmap, double *__restrict__ acc)
 {
-    __shared__ float sx[kSsimIn][kSsimIn], sy[kSsimIn][kSsimIn];
-    __shared__ float hm[5][kSsimIn][kSsimT];
+    // rows padded by one float: the passes' lane patterns then hit distinct banks
+    __shared__ float sx[kSsimIn][kSsimIn + 1], sy[kSsimIn][kSsimIn + 1];
+    __shared__ float hm[5][kSsimIn][kSsimT + 1];
     __shared__ float red[2][8];
     const int vc = blockIdx.z;                     // view * 3 + channel
     const size_t plane = (size_t)vc * W * H;
@@ -143,8 +144,8 @@ k_ssim_bwd(const float *__restrict__ img, const float *__restrict__ tgt, const f
            const float *__restrict__ amap, const float *__restrict__ bmap, const float *__restrict__ cmap,
            float *__restrict__ dl_dimg, float *__restrict__ dl_ddepth, double *__restrict__ acc)
 {
-    __shared__ float sa[3][kSsimIn][kSsimIn];
-    __shared__ float hb[3][kSsimIn][kSsimT];
+    __shared__ float sa[3][kSsimIn][kSsimIn + 1];
+    __shared__ float hb[3][kSsimIn][kSsimT + 1];
     __shared__ float red[8];
     const int vc = blockIdx.z, v = vc / 3, ch = vc % 3;
     const size_t plane = (size_t)vc * W * H;
@@ -182,6 +183,17 @@ k_ssim_bwd(const float *__restrict__ img, const float *__restrict__ tgt, const f
     float sD = 0.f;
     for (int i = threadIdx.x; i < kSsimT * (kSsimT / kRB); i += blockDim.x) {
         const int c = i % kSsimT, r0 = (i / kSsimT) * kRB;
+        const int gx = blockIdx.x * kSsimT + c;
+        // image and target of the thread's pixels, loaded before the blur so the loads overlap it
+        float xs[kRB], ys[kRB];
+#pragma unroll
+        for (int o = 0; o < kRB; o++) {
+            const int gy = blockIdx.y * kSsimT + r0 + o;
+            const bool in = gx < W && gy < H;
+            const size_t q = plane + (size_t)(in ? gy : 0) * W + (in ? gx : 0);
+            xs[o] = in ? img[q] : 0.f;
+            ys[o] = in ? tgt[q] : 0.f;
+        }
         float bl[3][kRB];
 #pragma unroll
         for (int m = 0; m < 3; m++) {
@@ -198,12 +210,11 @@ k_ssim_bwd(const float *__restrict__ img, const float *__restrict__ tgt, const f
         }
 #pragma unroll
         for (int o = 0; o < kRB; o++) {
-            const int r = r0 + o;
-            const int gx = blockIdx.x * kSsimT + c, gy = blockIdx.y * kSsimT + r;
+            const int gy = blockIdx.y * kSsimT + r0 + o;
             if (gx >= W || gy >= H) continue;
             const float ba = bl[0][o], bb = bl[1][o], bc = bl[2][o];
             const size_t q = plane + (size_t)gy * W + gx;
-            const float xv = img[q], yv = tgt[q];
+            const float xv = xs[o], yv = ys[o];
             const float sgn = xv > yv ? 1.f : (xv < yv ? -1.f : 0.f);
             dl_dimg[q] = wv * ((1.f - lam) * sgn / M - lam / M * (ba + 2.f * xv * bb + yv * bc));
             if (ch == 0 && dl_ddepth) {
