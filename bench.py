@@ -218,6 +218,23 @@ def workload_config(sc, extra=None):
 
 # ----------------------------------------------------------------------- ours
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of every rank's value (the job's timed region ends with its slowest rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps_per_rank: int, seconds: float) -> float:
+    """Whole-job window iterations/s: every rank runs its own window (replicas), so the job
+    completes world x steps windows in the slowest rank's time."""
+    return world * steps_per_rank / seconds
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -292,12 +309,8 @@ def main():
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    value = job_throughput(world, args.steps, ms_max / 1e3)
     st = win.read_status()
     if st[0] != 0:
         raise SystemExit(f"device status after timing: {st}")
@@ -361,9 +374,7 @@ def main():
     if not args.no_e2e:
         e2e = end_to_end(win, sc, cams, tgt_rgb, tgt_d, args, torch, N)
         if world > 1:
-            tt = torch.tensor([e2e["seconds"]], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e["value"] = world * e2e["steps"] / float(tt.item())
+            e2e["value"] = job_throughput(world, e2e["steps"], max_over_ranks(e2e["seconds"], world, dev))
 
     roof = None
     if stages:
