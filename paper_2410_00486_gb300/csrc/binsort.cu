@@ -359,6 +359,7 @@ k_sort_tiles(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ k
 {
     __shared__ uint64_t bufA[kSmallCap], bufB[kSmallCap];
     __shared__ uint32_t hist[kRsWarps][256];
+    __shared__ uint16_t lrank[kSmallCap];
     __shared__ uint32_t wsum[kRsWarps], wor[kRsWarps], wand[kRsWarps];
     const int64_t t = blockIdx.x;
     const uint32_t st = ranges[2 * t], en = ranges[2 * t + 1];
@@ -404,12 +405,20 @@ k_sort_tiles(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ k
         if (((vary >> shift) & 0xffu) == 0u) continue;      // block-uniform
         for (int i = lane; i < 256; i += 32) hist[w][i] = 0u;
         __syncwarp();
+        // count, and keep each key's rank among the equal digits of this warp's segment
+        // (earlier 32-key groups first, then lanes in order): the scatter below needs no
+        // ranking of its own
         for (uint32_t c = seg0; c < seg1; c += 32) {
             const uint32_t e = c + lane;
             const bool valid = e < seg1;
             const uint32_t d = valid ? ((uint32_t)(src[e] >> (32 + shift)) & 0xffu) : 0u;
             const unsigned peers = same_digit_lanes(d, __ballot_sync(kFull, valid));
-            if (valid && lane == __ffs(peers) - 1) hist[w][d] += __popc(peers);
+            const uint32_t before = valid ? hist[w][d] : 0u;
+            __syncwarp();
+            if (valid) {
+                lrank[e] = (uint16_t)(before + __popc(peers & ((1u << lane) - 1u)));
+                if (lane == __ffs(peers) - 1) hist[w][d] = before + __popc(peers);
+            }
             __syncwarp();
         }
         __syncthreads();
@@ -429,19 +438,10 @@ k_sort_tiles(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ k
             }
         }
         __syncthreads();
-        for (uint32_t c = seg0; c < seg1; c += 32) {
-            const uint32_t e = c + lane;
-            const bool valid = e < seg1;
-            const uint64_t k = valid ? src[e] : 0ull;
-            const uint32_t d = valid ? ((uint32_t)(k >> (32 + shift)) & 0xffu) : 0u;
-            const unsigned peers = same_digit_lanes(d, __ballot_sync(kFull, valid));
-            const uint32_t base = valid ? hist[w][d] : 0u;
-            __syncwarp();
-            if (valid) {
-                dst[base + __popc(peers & ((1u << lane) - 1u))] = k;
-                if (lane == __ffs(peers) - 1) hist[w][d] = base + __popc(peers);
-            }
-            __syncwarp();
+        for (uint32_t e = seg0 + lane; e < seg1; e += 32) {
+            const uint64_t k = src[e];
+            const uint32_t d = (uint32_t)(k >> (32 + shift)) & 0xffu;
+            dst[hist[w][d] + lrank[e]] = k;
         }
         __syncthreads();
         uint64_t *tmp = src;

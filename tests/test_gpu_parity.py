@@ -105,6 +105,7 @@ BIN_CASES = [
     (1, 500, 160, 120, 16, 30),
     (3, 2000, 200, 150, 8, 20),
     (2, 3000, 321, 247, 32, 60),
+    (1, 6000, 64, 48, 16, 10),       # lists of 1k-2k: the block-per-tile kernel
     (1, 12000, 64, 48, 16, 10),      # lists of 2k-16k: the large-bucket kernel
     (1, 40000, 32, 32, 16, 6),       # lists > 16k: the in-place global sort
 ]
