@@ -28,12 +28,17 @@ struct AdamArgs {
     float *loss_o;
 };
 
-__device__ __forceinline__ int group_of(int64_t i, const AdamArgs &a)
+// Learning rate of flat element i: its group's, chosen by comparisons with the group
+// starts (a select chain in registers, not an indexed load).
+__device__ __forceinline__ float lr_of(int64_t i, const AdamArgs &a)
 {
-    int gidx = 0;
-#pragma unroll
-    for (int k = 0; k < 5; k++) gidx += (i >= a.bnd[k]);
-    return gidx;
+    float lr = a.lr[0];
+    lr = i >= a.bnd[0] ? a.lr[1] : lr;
+    lr = i >= a.bnd[1] ? a.lr[2] : lr;
+    lr = i >= a.bnd[2] ? a.lr[3] : lr;
+    lr = i >= a.bnd[3] ? a.lr[4] : lr;
+    lr = i >= a.bnd[4] ? a.lr[5] : lr;
+    return lr;
 }
 
 // Bias corrections of the step held on the device, computed in double once per thread.
@@ -60,7 +65,7 @@ __device__ __forceinline__ float adam_elem(int64_t i, float p, float g, float &m
     v = fmaf(a.b2, v, (1.0f - a.b2) * g * g);
     const float mh = m * a.rbc1;
     const float denom = sqrtf(v) * a.rbc2sqrt + a.eps;
-    return p - a.lr[group_of(i, a)] * mh / denom;
+    return p - lr_of(i, a) * mh / denom;
 }
 
 __global__ void __launch_bounds__(256) k_adam_vec(AdamArgs a)
