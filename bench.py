@@ -540,8 +540,9 @@ def stage_breakdown(win, N, reps=5):
 
 
 def staging_pass(rec, bx0, bx1, by0, by1):
-    """The raster kernels' staging test (a splat is kept if its 1/255 iso-ellipse's bounding
-    box can reach the tile's pixel-centre box), in float32 on the records [k, 12]."""
+    """The raster kernels' staging test (a splat is kept if its alpha >= 1/255 ellipse can
+    reach the tile's pixel-centre box: bounding box first, then the ellipse's minimum of
+    q over the box), in float32 on the records [k, 12]."""
     import torch
     u, v, A, Bc, C, o = (rec[:, i] for i in range(6))
     keep = o * 255.0 >= 0.9999
@@ -551,7 +552,19 @@ def staging_pass(rec, bx0, bx1, by0, by1):
     ey = torch.sqrt(t2 * A / det) + 1e-2
     dx = (u - torch.minimum(torch.maximum(u, bx0), bx1)).abs()
     dy = (v - torch.minimum(torch.maximum(v, by0), by1)).abs()
-    return keep & (~(det > 0) | ((dx <= ex) & (dy <= ey)))
+    bbox = (dx <= ex) & (dy <= ey)
+    inside = (dx == 0) & (dy == 0)
+    qmin = torch.full_like(u, float("inf"))
+    for X in (bx0, bx1):
+        ddx = u - X
+        ddy = torch.minimum(torch.maximum(-(Bc / C) * ddx, v - by1), v - by0)
+        qmin = torch.minimum(qmin, A * ddx * ddx + 2.0 * Bc * ddx * ddy + C * ddy * ddy)
+    for Y in (by0, by1):
+        ddy = v - Y
+        ddx = torch.minimum(torch.maximum(-(Bc / A) * ddy, u - bx1), u - bx0)
+        qmin = torch.minimum(qmin, A * ddx * ddx + 2.0 * Bc * ddx * ddy + C * ddy * ddy)
+    touch = bbox & (inside | (qmin <= t2))
+    return keep & (~(det > 0) | touch)
 
 
 def backward_pairs(rec, vals, ranges, last, V, W, H, B, n_inst, chunk=1 << 23):

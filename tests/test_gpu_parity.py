@@ -1,6 +1,6 @@
 """Parity of every libcgs stage with the FP64 oracle on the same seeded inputs, called
 through the C ABI (GPU).  Sizes span several tiles and ragged tile tails; the
-workload-sized cases live in test_gpu_fullsize.py.
+workload-sized cases (the benchmark's window) live in test_gpu_fullsize.py.
 
 Tolerances: max |pixel| error 1e-4 (RGB, transmittance; depth relative to the
 scene's depth scale), gradient relative L2 error 1e-3 per parameter group; tile
@@ -220,9 +220,11 @@ def test_render_fwd_matches_oracle(name, bd):
     assert np.array_equal(out["vals"].cpu().numpy().view(np.uint32)[: len(vals)], vals)
     ok = fw["near"] == 0
     frac = 1.0 - ok.mean()
-    assert frac < 1e-2
+    assert frac < 2e-4
     img = out["img"].cpu().numpy()
-    e_img = np.abs(img - fw["img"]).max(1)[ok].max()
+    err = np.abs(img - fw["img"]).max(1)
+    assert (err > PIX_TOL).mean() < 1e-4
+    e_img = err[ok].max()
     e_T = np.abs(out["T"].cpu().numpy() - fw["T"])[ok].max()
     dscale = max(1.0, np.abs(fw["depth"]).max())
     e_d = (np.abs(out["depth"].cpu().numpy() - fw["depth"])[ok]).max() / dscale
@@ -324,14 +326,19 @@ def test_window_iteration_matches_oracle(name):
     torch.cuda.synchronize()
     assert win.read_status()[0] == 0
     it = O.iteration(sc.params, sc.n, sc.sh_degree, sc.cams, sc.width, sc.height, sc.tile, tgt_rgb, tgt_d,
-                     tol=1e-3)
+                     tol=1e-4)
     ok = it["fwd"]["near"] == 0
-    e_img = np.abs(win.img.cpu().numpy() - it["fwd"]["img"]).max(1)[ok].max()
+    err = np.abs(win.img.cpu().numpy() - it["fwd"]["img"]).max(1)
+    e_img = err[ok].max()
     assert e_img < PIX_TOL, e_img
+    # pixels where float32 and float64 took a different decision: fewer than 1e-4 of all,
+    # and every one of them flagged as near a threshold
+    assert (err > PIX_TOL).mean() < 1e-4
+    assert 1 - ok.mean() < 1e-3
     np.testing.assert_allclose(win.loss_view.cpu().numpy(), it["fwd"]["loss_view"], rtol=1e-4)
     gg = win.grads.cpu().numpy().astype(np.float64)
     errs = {k: rel_l2(gg[sl], it["grads"][sl]) for k, sl in group_slices(sc.n, sc.sh_degree).items()}
-    print(f"[iter {name}] excluded px {1 - ok.mean():.2e} max|dimg| {e_img:.2e} " +
+    print(f"[iter {name}] excluded px {1 - ok.mean():.2e} flipped {(err > PIX_TOL).mean():.2e} max|dimg| {e_img:.2e} " +
           " ".join(f"{k}:{e:.1e}" for k, e in errs.items()))
     for k, e in errs.items():
         assert e < GRAD_REL_TOL, (k, e)
@@ -761,7 +768,7 @@ def test_window_ssim_iteration_matches_oracle(name):
     torch.cuda.synchronize()
     assert win.read_status()[0] == 0
     it = O.iteration(sc.params, sc.n, sc.sh_degree, sc.cams, sc.width, sc.height, sc.tile, tgt_rgb, tgt_d,
-                     tol=1e-3, lambda_ssim=0.2)
+                     tol=1e-4, lambda_ssim=0.2)
     np.testing.assert_allclose(win.loss_view.cpu().numpy(), it["loss_view"], rtol=1e-4)
     gg = win.grads.cpu().numpy().astype(np.float64)
     errs = {k: rel_l2(gg[sl], it["grads"][sl]) for k, sl in group_slices(sc.n, sc.sh_degree).items()}
