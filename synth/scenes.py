@@ -297,6 +297,26 @@ def make_records(seed: int, views: int, n: int, W: int, H: int, cull_frac: float
     return u, v, radius, z
 
 
+def make_conics(seed: int, radius, opacity_low: float = 0.002):
+    """Per record an inverse covariance (A, B, C), float32: an ellipse whose larger
+    3-sigma half-axis is about the record's radius, random aspect (0.05-1) and rotation;
+    and an opacity, uniform in [opacity_low, 0.99] (some below 1/255)."""
+    rng = np.random.default_rng(seed)
+    r = np.maximum(np.asarray(radius, np.float64), 1.0)
+    m = r.size
+    lmax = (r / 3.0) ** 2
+    lmin = lmax * rng.uniform(0.05, 1.0, m)
+    th = rng.uniform(0, np.pi, m)
+    c, s = np.cos(th), np.sin(th)
+    sxx = c * c * lmax + s * s * lmin
+    syy = s * s * lmax + c * c * lmin
+    sxy = c * s * (lmax - lmin)
+    det = sxx * syy - sxy * sxy
+    conic = np.stack([syy / det, -sxy / det, sxx / det], 1).astype(np.float32)
+    opacity = rng.uniform(opacity_low, 0.99, m).astype(np.float32)
+    return conic, opacity
+
+
 def make_point_cloud(seed: int, m: int, dup_frac: float = 0.01, outliers: int = 2):
     """A keyframe's coloured point cloud for geometric densification: m points of the
     6x5x3 m room (surfaces and interior as the room scenes), float32 xyz and rgb in [0, 1].

@@ -46,6 +46,10 @@ MUTATIONS = [
      [TG.test_densify_stats_hand_example]),
     ("if (acc < 0.0) { acc = 0.0;", "if (0) { acc = 0.0;",
      [TP.test_sh_degree0_colour_is_view_independent_and_clamped]),
+    ("float bc = B / C, ba = B / A, B2 = 2.0f * B;", "float bc = B / C, ba = B / A, B2 = B;",
+     [lambda: TR.test_bin_lists_with_reach_test_brute_force(0)]),
+    ("float ddy = fminf(fmaxf(-(bc * ddx), v - by1), v - by0);", "float ddy = fminf(fmaxf(bc * ddx, v - by1), v - by0);",
+     [lambda: TR.test_bin_lists_with_reach_test_brute_force(1)]),
 ]
 
 
