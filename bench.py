@@ -530,73 +530,13 @@ def stage_breakdown(win, N, reps=5):
     rad = win.rec.view(torch.int32).view(-1, 12)[:, 7]
     work = {
         "pairs_fwd_eval": float(part[:, 3].sum()), "pairs_blend": float(part[:, 4].sum()),
-        "pairs_bwd_eval": backward_pairs(win.rec, win.vals, win.ranges, win.last, win.V, win.W, win.H,
-                                         win.cfg.tile, int(win.n_inst.item())),
-        "sum_last": float(win.last.double().sum()),
+        # every entry of a tile's list is staged (the binning keeps only splats that reach the
+        # tile), so the backward evaluates each pixel's list up to its `last`
+        "pairs_bwd_eval": float(win.last.double().sum()),
         "visible_slots": int((rad > 0).sum().item()), "instances": int(win.n_inst.item()),
         "params": win.P, "n": win.n, "slots": win.V * win.n, "pixels": win.V * win.W * win.H, "tiles": win.Ttot,
     }
     return {k: round(v, 4) for k, v in acc.items()}, work
-
-
-def staging_pass(rec, bx0, bx1, by0, by1):
-    """The raster kernels' staging test (a splat is kept if its alpha >= 1/255 ellipse can
-    reach the tile's pixel-centre box: bounding box first, then the ellipse's minimum of
-    q over the box), in float32 on the records [k, 12]."""
-    import torch
-    u, v, A, Bc, C, o = (rec[:, i] for i in range(6))
-    keep = o * 255.0 >= 0.9999
-    det = A * C - Bc * Bc
-    t2 = 2.0 * torch.log(255.0 * o) * 1.001 + 1e-3
-    ex = torch.sqrt(t2 * C / det) + 1e-2
-    ey = torch.sqrt(t2 * A / det) + 1e-2
-    dx = (u - torch.minimum(torch.maximum(u, bx0), bx1)).abs()
-    dy = (v - torch.minimum(torch.maximum(v, by0), by1)).abs()
-    bbox = (dx <= ex) & (dy <= ey)
-    inside = (dx == 0) & (dy == 0)
-    qmin = torch.full_like(u, float("inf"))
-    for X in (bx0, bx1):
-        ddx = u - X
-        ddy = torch.minimum(torch.maximum(-(Bc / C) * ddx, v - by1), v - by0)
-        qmin = torch.minimum(qmin, A * ddx * ddx + 2.0 * Bc * ddx * ddy + C * ddy * ddy)
-    for Y in (by0, by1):
-        ddy = v - Y
-        ddx = torch.minimum(torch.maximum(-(Bc / A) * ddy, u - bx1), u - bx0)
-        qmin = torch.minimum(qmin, A * ddx * ddx + 2.0 * Bc * ddx * ddy + C * ddy * ddy)
-    touch = bbox & (inside | (qmin <= t2))
-    return keep & (~(det > 0) | touch)
-
-
-def backward_pairs(rec, vals, ranges, last, V, W, H, B, n_inst, chunk=1 << 23):
-    """(pixel, splat) pairs the raster backward evaluates: for every pixel, the splats of its
-    tile's list before its `last` position that pass the staging test.  A prefix sum of the
-    pass flags over the tile lists turns this into one gather per pixel (measurement only)."""
-    import torch
-    dev = rec.device
-    Tx, Ty = -(-W // B), -(-H // B)
-    rg = ranges.view(-1, 2).long() & 0xFFFFFFFF
-    start, end = rg[:, 0], rg[:, 1]
-    recs = rec.view(-1, 12)
-    ids = vals[:n_inst].long() & 0xFFFFFFFF
-    tile_of = torch.repeat_interleave(torch.arange(rg.shape[0], device=dev), end - start)
-    passed = torch.empty(n_inst, dtype=torch.int64, device=dev)
-    for c0 in range(0, n_inst, chunk):
-        c1 = min(n_inst, c0 + chunk)
-        t = tile_of[c0:c1] % (Tx * Ty)
-        tx, ty = t % Tx, t // Tx
-        bx0 = (tx * B).float()
-        bx1 = (torch.clamp(tx * B + B, max=W) - 1).float()
-        by0 = (ty * B).float()
-        by1 = (torch.clamp(ty * B + B, max=H) - 1).float()
-        passed[c0:c1] = staging_pass(recs[ids[c0:c1]], bx0, bx1, by0, by1).long()
-    cum = torch.zeros(n_inst + 1, dtype=torch.int64, device=dev)
-    cum[1:] = torch.cumsum(passed, 0)
-    yy, xx = torch.meshgrid(torch.arange(H, device=dev), torch.arange(W, device=dev), indexing="ij")
-    tpix = (yy // B) * Tx + (xx // B)
-    tglob = (torch.arange(V, device=dev)[:, None, None] * (Tx * Ty) + tpix[None]).reshape(-1)
-    st = start[tglob]
-    lst = last.reshape(-1).long()
-    return float((cum[st + lst] - cum[st]).sum().item())
 
 
 def hbm_bytes(stage, w):
@@ -677,7 +617,7 @@ def roofline(stages, work, clocks):
         return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Top/s",
                 "frac": ach / peak, "traffic": traffic,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (FP32 instructions/s), derived",
-                "work": {k: work[k] for k in ("pairs_fwd_eval", "pairs_bwd_eval", "pairs_blend", "sum_last")},
+                "work": {k: work[k] for k in ("pairs_fwd_eval", "pairs_bwd_eval", "pairs_blend")},
                 "ops_per_pair": {"fwd_eval": FWD_OPS_EVAL, "fwd_blend": FWD_OPS_BLEND, "bwd_eval": BWD_OPS_EVAL,
                                  "bwd_blend": BWD_OPS_BLEND}}
     b = hbm_bytes(dom, work)

@@ -35,7 +35,7 @@
  *    [0] u  [1] v      projected centre, pixel (x, y) centred on integer (x, y)
  *    [2] A  [3] B  [4] C   conic (inverse 2-D covariance): power = -(A dx^2 + C dy^2)/2 - B dx dy
  *    [5] opacity  [6] depth (camera z)  [7] radius as int32 bits (0 = culled)
- *    [8] r  [9] g  [10] b  [11] colour clamp mask as int32 bits (bit c = channel c clamped)
+ *    [8] r  [9] g  [10] b  [11] tau = -ln(255 opacity): alpha >= 1/255 exactly when power >= tau
  * Slot gradient (device float[V*n][CGS_REC_FLOATS]): dL/d(field) at the same
  * index for fields 0-6 and 8-10; entries 7 and 11 are unused (kept zero).
  */
@@ -116,18 +116,26 @@ int cgs_preprocess(const float *params, int64_t n, const cgs_camera *cams, int32
 
 /*
  * cgs_bin_sort -- tile binning: every visible slot is listed in each tile of its
- * rectangle, and each tile's list is sorted by (depth, slot) ascending; tiles are
+ * rectangle that its alpha >= 1/255 ellipse can reach at a pixel centre (a splat left out
+ * of a tile is one every pixel of the tile skips: the render is unchanged), and each
+ * tile's list is sorted by (depth, slot) ascending; tiles are
  * numbered view-major (global tile = v*Tx*Ty + ty*Tx + tx), so the whole window
  * shares one sort.  The order is the blending order of Eq. 1 (front to back);
  * equal depths keep the Gaussian order.  Rectangle of a slot with centre (u, v)
  * and radius r, in tile units, hi exclusive:
  *   [clamp(floor((u-r)/B), 0, Tx), clamp(floor((u+r+B-1)/B), 0, Tx)) and likewise in y,
- * evaluated exactly (u enters only through floor(u)).
+ * evaluated exactly (u enters only through floor(u)).  Reach of a splat in the tile's
+ * pixel-centre box [bx0, bx1] x [by0, by1], from the record's conic and tau in float32,
+ * every operation one IEEE rounding: none if tau > 1e-4; all if A C - B B <= 0;
+ * otherwise, with q = A dx^2 + 2 B dx dy + C dy^2 and t2 = (-2 tau) 1.001 + 1e-3, the
+ * ellipse's bounding box (half-extents sqrt(t2 C / det) + 0.01, sqrt(t2 A / det) + 0.01)
+ * must meet the box and, unless the centre is inside it, the minimum of q over the box
+ * (on an edge: the parabola's clamped vertex) must be at most t2.
  * Method: a counting pass over tiles (the most significant radix digit, one per
  * tile), a scatter into per-tile buckets, then a per-tile sort of the unique
  * 64-bit keys (depth bits << 32 | slot) in shared memory.
- *   rec        device, records from cgs_preprocess (u, v, depth, radius are read)
- *   workspace  device scratch of at least cgs_bin_sort_workspace(capacity, V, cfg) bytes,
+ *   rec        device, records from cgs_preprocess (u, v, conic, depth, radius, tau are read)
+ *   workspace  device scratch of at least cgs_bin_sort_workspace(capacity, n, V, cfg) bytes,
  *              256-byte aligned
  *   capacity   number of entries `vals` can hold
  *   vals       device out, uint32[capacity]: slot ids, tile after tile
@@ -138,7 +146,7 @@ int cgs_preprocess(const float *params, int64_t n, const cgs_camera *cams, int32
  *   n_inst_dev device out, int64: total number of tile instances (also when it
  *              exceeds capacity; then lists are truncated and CGS_ERR_CAPACITY set)
  */
-size_t cgs_bin_sort_workspace(int64_t capacity, int32_t V, const cgs_config *cfg);
+size_t cgs_bin_sort_workspace(int64_t capacity, int64_t n, int32_t V, const cgs_config *cfg);
 int cgs_bin_sort(const float *rec, int64_t n, int32_t V, const cgs_config *cfg, void *workspace,
                  size_t workspace_bytes, int64_t capacity, uint32_t *vals, uint32_t *ranges,
                  uint32_t *tile_order, int64_t *n_inst_dev, int32_t *status_dev, void *stream);

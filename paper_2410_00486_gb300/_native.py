@@ -54,7 +54,7 @@ _SIGS = {
     "cgs_param_count": (c_int64, [c_int64, c_int32]),
     "cgs_tiles_per_view": (c_int64, [_P]),
     "cgs_preprocess": (c_int32, [_P, c_int64, _P, c_int32, _P, _P, _P, _P, _P]),
-    "cgs_bin_sort_workspace": (c_size_t, [c_int64, c_int32, _P]),
+    "cgs_bin_sort_workspace": (c_size_t, [c_int64, c_int64, c_int32, _P]),
     "cgs_bin_sort": (c_int32, [_P, c_int64, c_int32, _P, _P, c_size_t, c_int64, _P, _P, _P, _P, _P, _P]),
     "cgs_render_fwd_workspace": (c_size_t, [c_int32, _P]),
     "cgs_render_fwd": (c_int32, [_P, _P, _P, _P, c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
@@ -162,8 +162,8 @@ def cgs_preprocess(params, n, cams, V, cfg, rec, slot_grad=None, status=None, st
                                                   _dev(slot_grad), _dev(status), _stream(stream)))
 
 
-def cgs_bin_sort_workspace(capacity, V, cfg) -> int:
-    return lib().cgs_bin_sort_workspace(capacity, V, byref(cfg))
+def cgs_bin_sort_workspace(capacity, n, V, cfg) -> int:
+    return lib().cgs_bin_sort_workspace(capacity, n, V, byref(cfg))
 
 
 def cgs_bin_sort(rec, n, V, cfg, workspace, capacity, vals, ranges, tile_order, n_inst, status=None,

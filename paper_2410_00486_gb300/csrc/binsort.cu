@@ -28,22 +28,26 @@ constexpr int kBigThreads = 1024;
 constexpr int kBigCap = 16384;       // keys held in shared memory by the big-tile kernel
 constexpr uint64_t kPadKey = ~0ull;  // larger than any real key
 constexpr size_t kAggMaxSmem = 96 * 1024;   // per-view tile histogram in shared memory
+constexpr int kChunk = 4096;                // slots of a view per block of the count and scatter passes
 
 struct BinWs {
     uint32_t *count;     // [Ttot + 1]
     uint32_t *cursor;    // [Ttot]
     uint32_t *nbig;      // [1]
     uint32_t *big;       // [Ttot]
+    uint32_t *bcount;    // [chunks x Ttot]: per (slot chunk, tile) instance counts
     uint64_t *keys;      // [capacity]
 };
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Sections: counters (one memset), big-tile list, keys.
-static size_t ws_layout(int64_t capacity, int64_t Ttot, BinWs *w, void *base)
+// Sections: counters (one memset), big-tile list, per-chunk counts (shared-memory path
+// only), keys.
+static size_t ws_layout(int64_t capacity, int64_t Ttot, int64_t chunk_counts, BinWs *w, void *base)
 {
     size_t head = align256(sizeof(uint32_t) * (2 * (size_t)Ttot + 2));
     size_t bigb = align256(sizeof(uint32_t) * (size_t)Ttot);
+    size_t chb = align256(sizeof(uint32_t) * (size_t)chunk_counts);
     size_t keyb = align256(sizeof(uint64_t) * (size_t)(capacity > 0 ? capacity : 1));
     if (w && base) {
         char *b = static_cast<char *>(base);
@@ -51,12 +55,24 @@ static size_t ws_layout(int64_t capacity, int64_t Ttot, BinWs *w, void *base)
         w->cursor = w->count + Ttot + 1;
         w->nbig = w->cursor + Ttot;
         w->big = reinterpret_cast<uint32_t *>(b + head);
-        w->keys = reinterpret_cast<uint64_t *>(b + head + bigb);
+        w->bcount = reinterpret_cast<uint32_t *>(b + head + bigb);
+        w->keys = reinterpret_cast<uint64_t *>(b + head + bigb + chb);
     }
-    return head + bigb + keyb;
+    return head + bigb + chb + keyb;
 }
 
-size_t bin_ws_bytes(int64_t capacity, int64_t Ttot) { return ws_layout(capacity, Ttot, nullptr, nullptr); }
+// Per-(chunk, tile) counts kept between the count and scatter passes when a view's tile
+// histogram fits in shared memory.
+static int64_t chunk_count_entries(int64_t n, int64_t V, int64_t Tv)
+{
+    if (sizeof(uint32_t) * (size_t)Tv > kAggMaxSmem) return 0;
+    return (n + kChunk - 1) / kChunk * V * Tv;
+}
+
+size_t bin_ws_bytes(int64_t capacity, int64_t n, int64_t V, int64_t Tv)
+{
+    return ws_layout(capacity, Tv * V, chunk_count_entries(n, V, Tv), nullptr, nullptr);
+}
 
 __device__ __forceinline__ bool load_slot(const float4 *__restrict__ rec, int64_t slot, float &u, float &v,
                                           float &z, int &r)
@@ -71,6 +87,21 @@ __device__ __forceinline__ bool load_slot(const float4 *__restrict__ rec, int64_
     return true;
 }
 
+// The per-slot part of the tile reach test (record fields 2, 3, 4: conic; 11: tau).
+__device__ __forceinline__ ReachPre load_reach(const float4 *__restrict__ rec, int64_t slot)
+{
+    const float *rf = reinterpret_cast<const float *>(rec + kRec4 * slot);
+    return reach_prepare(__ldg(rf + 2), __ldg(rf + 3), __ldg(rf + 4), __ldg(rf + 11));
+}
+
+// Does the slot (centre u, v) belong in tile (tx, ty): can it reach alpha >= 1/255 there?
+__device__ __forceinline__ bool in_tile(const ReachPre &e, float u, float v, int tx, int ty, const Grid &g)
+{
+    const float bx0 = (float)(tx * g.B), bx1 = (float)(min(tx * g.B + g.B, g.W) - 1);
+    const float by0 = (float)(ty * g.B), by1 = (float)(min(ty * g.B + g.B, g.H) - 1);
+    return reach_box(e, u, v, bx0, bx1, by0, by1);
+}
+
 __global__ void k_count(const float4 *__restrict__ rec, int64_t n, int V, Grid g, uint32_t *__restrict__ count)
 {
     const int64_t total = (int64_t)V * n;
@@ -80,20 +111,22 @@ __global__ void k_count(const float4 *__restrict__ rec, int64_t n, int V, Grid g
         if (!load_slot(rec, s, u, v, z, r)) continue;
         const int64_t view = s / n;
         Rect R = tile_rect(u, v, r, g);
+        const ReachPre e = load_reach(rec, s);
         uint32_t *base = count + view * g.Tv;
         for (int ty = R.y0; ty < R.y1; ty++)
-            for (int tx = R.x0; tx < R.x1; tx++) atomicAdd(base + ty * g.Tx + tx, 1u);
+            for (int tx = R.x0; tx < R.x1; tx++)
+                if (in_tile(e, u, v, tx, ty, g)) atomicAdd(base + ty * g.Tx + tx, 1u);
     }
 }
 
 // Shared-memory aggregated variants, used when a view's tile histogram fits in shared
 // memory: block (c, v) owns slots [c*kChunk, (c+1)*kChunk) of view v, counts its
 // instances per tile in shared memory and touches each global counter once.
-constexpr int kChunk = 4096;
 constexpr int kAggThreads = 512;
 
-// Calls f(ty, x0, x1, key) for every tile row [x0, x1) x {ty} of the rectangles of the
-// visible slots [s0, s1) of a view, load-balanced over the lanes of each warp: a warp
+// Calls f(tile in view, key) for every tile of the rectangles of the visible slots [s0, s1)
+// of a view that the slot can reach (in_tile), row by row, load-balanced over the lanes of
+// each warp: a warp
 // takes 32 slots, forms the prefix sum of their row counts, and hands out rows
 // round-robin; a lane finds the slot owning row j by a 5-step binary search over the
 // prefix (shuffles).  Slot order within a warp is kept, so a warp's calls for one tile
@@ -107,7 +140,8 @@ __device__ __forceinline__ void for_each_tile_row(const float4 *__restrict__ rec
         const int64_t gi = wb + lane;
         int h = 0, x0 = 0, x1 = 0, y0 = 0;
         uint32_t zb = 0;
-        float u, v, z;
+        float u = 0.f, v = 0.f, z;
+        ReachPre e{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
         int r;
         if (gi < s1 && load_slot(rec, (int64_t)view * n + gi, u, v, z, r)) {
             const Rect R = tile_rect(u, v, r, g);
@@ -117,6 +151,7 @@ __device__ __forceinline__ void for_each_tile_row(const float4 *__restrict__ rec
                 x1 = R.x1;
                 y0 = R.y0;
                 zb = __float_as_uint(z);
+                e = load_reach(rec, (int64_t)view * n + gi);
             }
         }
         int incl = h;
@@ -136,16 +171,24 @@ __device__ __forceinline__ void for_each_tile_row(const float4 *__restrict__ rec
             const int ox0 = __shfl_sync(kFull, x0, L), ox1 = __shfl_sync(kFull, x1, L);
             const int oy0 = __shfl_sync(kFull, y0, L);
             const uint32_t ozb = __shfl_sync(kFull, zb, L);
+            const float ou = __shfl_sync(kFull, u, L), ov = __shfl_sync(kFull, v, L);
+            const ReachPre oe{__shfl_sync(kFull, e.A, L),  __shfl_sync(kFull, e.B2, L), __shfl_sync(kFull, e.C, L),
+                              __shfl_sync(kFull, e.t2, L), __shfl_sync(kFull, e.ex, L), __shfl_sync(kFull, e.ey, L),
+                              __shfl_sync(kFull, e.bc, L), __shfl_sync(kFull, e.ba, L), __shfl_sync(kFull, e.mode, L)};
             if (j < total) {
                 const uint32_t slot = (uint32_t)((int64_t)view * n + wb + L);
-                f(oy0 + (j - (oend - oh)), ox0, ox1, ((uint64_t)ozb << 32) | (uint64_t)slot);
+                const uint64_t key = ((uint64_t)ozb << 32) | (uint64_t)slot;
+                const int ty = oy0 + (j - (oend - oh));
+                for (int tx = ox0; tx < ox1; tx++)
+                    if (in_tile(oe, ou, ov, tx, ty, g)) f(ty * g.Tx + tx, key);
             }
         }
     }
 }
 
 __global__ void __launch_bounds__(kAggThreads)
-k_count_agg(const float4 *__restrict__ rec, int64_t n, Grid g, uint32_t *__restrict__ count)
+k_count_agg(const float4 *__restrict__ rec, int64_t n, Grid g, uint32_t *__restrict__ count,
+            uint32_t *__restrict__ bcount)
 {
     extern __shared__ uint32_t hist[];
     const int view = blockIdx.y;
@@ -153,13 +196,15 @@ k_count_agg(const float4 *__restrict__ rec, int64_t n, Grid g, uint32_t *__restr
     const int64_t s1 = min(n, s0 + kChunk);
     for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) hist[t] = 0;
     __syncthreads();
-    for_each_tile_row(rec, n, view, s0, s1, g, [&](int ty, int x0, int x1, uint64_t) {
-        for (int tx = x0; tx < x1; tx++) atomicAdd(&hist[ty * g.Tx + tx], 1u);
-    });
+    for_each_tile_row(rec, n, view, s0, s1, g, [&](int t, uint64_t) { atomicAdd(&hist[t], 1u); });
     __syncthreads();
     uint32_t *base = count + (int64_t)view * g.Tv;
-    for (int t = threadIdx.x; t < g.Tv; t += blockDim.x)
-        if (hist[t]) atomicAdd(base + t, hist[t]);
+    uint32_t *mine = bcount + ((int64_t)view * gridDim.x + blockIdx.x) * g.Tv;
+    for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) {
+        const uint32_t c = hist[t];
+        mine[t] = c;
+        if (c) atomicAdd(base + t, c);
+    }
 }
 
 // Single-block exclusive scan of the per-tile counts; writes ranges (clamped to the
@@ -227,8 +272,10 @@ __global__ void k_scatter(const float4 *__restrict__ rec, int64_t n, int V, Grid
         const int64_t view = s / n;
         Rect R = tile_rect(u, v, r, g);
         const uint64_t key = ((uint64_t)__float_as_uint(z) << 32) | (uint64_t)(uint32_t)s;
+        const ReachPre e = load_reach(rec, s);
         for (int ty = R.y0; ty < R.y1; ty++)
             for (int tx = R.x0; tx < R.x1; tx++) {
+                if (!in_tile(e, u, v, tx, ty, g)) continue;
                 const int64_t t = view * g.Tv + ty * g.Tx + tx;
                 const uint64_t pos = (uint64_t)start[t] + atomicAdd(cursor + t, 1u);
                 if (pos < (uint64_t)capacity) keys[pos] = key;
@@ -241,29 +288,24 @@ __global__ void k_scatter(const float4 *__restrict__ rec, int64_t n, int V, Grid
 // single global atomic, then places its instances with shared-memory atomics.
 __global__ void __launch_bounds__(kAggThreads)
 k_scatter_agg(const float4 *__restrict__ rec, int64_t n, Grid g, const uint32_t *__restrict__ start,
-              uint32_t *__restrict__ cursor, uint64_t *__restrict__ keys, int64_t capacity)
+              uint32_t *__restrict__ cursor, const uint32_t *__restrict__ bcount, uint64_t *__restrict__ keys,
+              int64_t capacity)
 {
     extern __shared__ uint32_t hist[];     // [Tv] counts, then run positions
     const int view = blockIdx.y;
     const int64_t s0 = (int64_t)blockIdx.x * kChunk;
     const int64_t s1 = min(n, s0 + kChunk);
-    for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) hist[t] = 0;
-    __syncthreads();
-    for_each_tile_row(rec, n, view, s0, s1, g, [&](int ty, int x0, int x1, uint64_t) {
-        for (int tx = x0; tx < x1; tx++) atomicAdd(&hist[ty * g.Tx + tx], 1u);
-    });
-    __syncthreads();
+    // this chunk's per-tile counts (from the count pass): reserve one run per tile
     const int64_t tbase = (int64_t)view * g.Tv;
+    const uint32_t *mine = bcount + ((int64_t)view * gridDim.x + blockIdx.x) * g.Tv;
     for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) {
-        const uint32_t c = hist[t];
-        if (c) hist[t] = start[tbase + t] + atomicAdd(cursor + tbase + t, c);
+        const uint32_t c = mine[t];
+        hist[t] = c ? start[tbase + t] + atomicAdd(cursor + tbase + t, c) : 0u;
     }
     __syncthreads();
-    for_each_tile_row(rec, n, view, s0, s1, g, [&](int ty, int x0, int x1, uint64_t key) {
-        for (int tx = x0; tx < x1; tx++) {
-            const uint64_t pos = atomicAdd(&hist[ty * g.Tx + tx], 1u);
-            if (pos < (uint64_t)capacity) keys[pos] = key;
-        }
+    for_each_tile_row(rec, n, view, s0, s1, g, [&](int t, uint64_t key) {
+        const uint64_t pos = atomicAdd(&hist[t], 1u);
+        if (pos < (uint64_t)capacity) keys[pos] = key;
     });
 }
 
@@ -571,7 +613,7 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
 {
     const int64_t Ttot = g.Tv * V;
     BinWs w;
-    ws_layout(capacity, Ttot, &w, ws);
+    ws_layout(capacity, Ttot, chunk_count_entries(n, V, g.Tv), &w, ws);
     const float4 *r4 = reinterpret_cast<const float4 *>(rec);
     cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (2 * (size_t)Ttot + 2), s);
     if (e != cudaSuccess) return e;
@@ -588,12 +630,13 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((slots + threads - 1) / threads, (int64_t)num_sms * 16);
     if (agg)
-        k_count_agg<<<agrid, kAggThreads, hist_bytes, s>>>(r4, n, g, w.count);
+        k_count_agg<<<agrid, kAggThreads, hist_bytes, s>>>(r4, n, g, w.count, w.bcount);
     else
         k_count<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count);
     k_scan<<<1, 1024, 0, s>>>(w.count, Ttot, capacity, ranges, n_inst, status);
     if (agg)
-        k_scatter_agg<<<agrid, kAggThreads, hist_bytes, s>>>(r4, n, g, w.count, w.cursor, w.keys, capacity);
+        k_scatter_agg<<<agrid, kAggThreads, hist_bytes, s>>>(r4, n, g, w.count, w.cursor, w.bcount, w.keys,
+                                                             capacity);
     else
         k_scatter<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count, w.cursor, w.keys, capacity);
     k_sort_tiles<<<(unsigned)Ttot, kRsThreads, 0, s>>>(ranges, w.keys, vals, w.big, w.nbig);

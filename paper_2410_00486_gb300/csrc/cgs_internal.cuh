@@ -81,6 +81,70 @@ __device__ __forceinline__ Rect tile_rect(float u, float v, int r, const Grid &g
     return R;
 }
 
+// Whether a projected splat can reach alpha >= 1/255 at a pixel centre of the box
+// [bx0, bx1] x [by0, by1]: tile lists keep a slot only in such tiles of its rect.  Every
+// operation is one IEEE rounding (explicit intrinsics, no contraction), so the decision is
+// a fixed function of the float32 record: tau = -ln(255 o) > 1e-4 (o < 1/255, with a
+// margin) reaches nothing; det <= 0 reaches everything; otherwise alpha >= 1/255 needs
+// q = A dx^2 + 2 B dx dy + C dy^2 <= -2 tau, widened to t2 = (-2 tau) 1.001 + 1e-3.  The
+// ellipse's bounding box (half-extents sqrt(t2 C / det) + 0.01, sqrt(t2 A / det) + 0.01)
+// is tested first; then, with the centre outside the box, the minimum of q over the box,
+// which lies on an edge where q is a parabola minimised at its clamped vertex.  The
+// margins exceed the float32 error of the raster's per-pixel test (power < tau skips), so
+// a splat left out of a tile is one every pixel of the tile would skip.
+__device__ __forceinline__ float edge_q(float A, float B2, float C, float ddx, float ddy)
+{
+    return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, ddx), ddx), __fmul_rn(__fmul_rn(B2, ddx), ddy)),
+                     __fmul_rn(__fmul_rn(C, ddy), ddy));
+}
+
+// The per-splat part of the reach test (one division and square root each), computed once
+// per slot; reach_box finishes it for a box.
+struct ReachPre {
+    float A, B2, C, t2, ex, ey, bc, ba;
+    int mode;   // 0 reaches nothing, 1 reaches everything, 2 test the box
+};
+__device__ __forceinline__ ReachPre reach_prepare(float A, float B, float C, float tau)
+{
+    ReachPre p{A, __fmul_rn(2.f, B), C, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+    if (!(tau <= 1e-4f)) return p;
+    const float det = __fsub_rn(__fmul_rn(A, C), __fmul_rn(B, B));
+    if (!(det > 0.f)) {
+        p.mode = 1;
+        return p;
+    }
+    p.mode = 2;
+    p.t2 = __fadd_rn(__fmul_rn(__fmul_rn(-2.f, tau), 1.001f), 1e-3f);
+    p.ex = __fadd_rn(__fsqrt_rn(__fdiv_rn(__fmul_rn(p.t2, C), det)), 1e-2f);
+    p.ey = __fadd_rn(__fsqrt_rn(__fdiv_rn(__fmul_rn(p.t2, A), det)), 1e-2f);
+    p.bc = __fdiv_rn(B, C);
+    p.ba = __fdiv_rn(B, A);
+    return p;
+}
+__device__ __forceinline__ bool reach_box(const ReachPre &p, float u, float v, float bx0, float bx1, float by0,
+                                          float by1)
+{
+    if (p.mode != 2) return p.mode == 1;
+    const float dx = fabsf(__fsub_rn(u, fminf(fmaxf(u, bx0), bx1)));
+    const float dy = fabsf(__fsub_rn(v, fminf(fmaxf(v, by0), by1)));
+    if (!(dx <= p.ex && dy <= p.ey)) return false;
+    if (dx == 0.f && dy == 0.f) return true;
+    float qmin = __int_as_float(0x7f800000);   // +infinity
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+        const float ddx = __fsub_rn(u, e ? bx1 : bx0);
+        const float ddy = fminf(fmaxf(-__fmul_rn(p.bc, ddx), __fsub_rn(v, by1)), __fsub_rn(v, by0));
+        qmin = fminf(qmin, edge_q(p.A, p.B2, p.C, ddx, ddy));
+    }
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+        const float ddy = __fsub_rn(v, e ? by1 : by0);
+        const float ddx = fminf(fmaxf(-__fmul_rn(p.ba, ddy), __fsub_rn(u, bx1)), __fsub_rn(u, bx0));
+        qmin = fminf(qmin, edge_q(p.A, p.B2, p.C, ddx, ddy));
+    }
+    return qmin <= p.t2;
+}
+
 // Exponent of the projected 2-D Gaussian at a pixel, written with explicit
 // roundings so the forward and backward kernels take bit-identical decisions:
 //   power = dx (-A/2 dx - B dy) + (-C/2 dy) dy,  (dx, dy) = (u - x, v - y).

@@ -302,7 +302,9 @@ k_preprocess(const float *__restrict__ P, int64_t n, const cgs_camera *__restric
         }
         r[0] = make_float4(o.u, o.v, o.A, o.B);
         r[1] = make_float4(o.C, o.o, o.t[2], __int_as_float(o.radius));
-        r[2] = make_float4(o.rgb[0], o.rgb[1], o.rgb[2], __int_as_float(o.mask));
+        // tau = -ln(255 o): alpha >= 1/255 exactly when power >= tau (the tile test and the
+        // raster kernels' exponent threshold)
+        r[2] = make_float4(o.rgb[0], o.rgb[1], o.rgb[2], -logf(255.0f * o.o));
         if (sgrad) {
             float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
             float4 *gp = sgrad + kRec4 * slot;

@@ -57,52 +57,6 @@ __device__ __forceinline__ void item_tile(const uint32_t *order, const Grid &g, 
     tx = t - ty * g.Tx;
 }
 
-// Conservative tile test of a staged splat: can it reach alpha >= 1/255 at any pixel
-// centre of the box [bx0, bx1] x [by0, by1]?  alpha = o exp(power) <= o (power <= 0), so
-// a splat with o < 1/255 is skipped by every pixel; otherwise alpha >= 1/255 needs
-// q = d^T Q d <= 2 ln(255 o), an ellipse whose axis-aligned half-extents are
-// sqrt(2 ln(255 o) (Q^-1)_xx) and sqrt(2 ln(255 o) (Q^-1)_yy), (Q^-1)_xx = C/det(Q).
-// After that bounding-box reject, the ellipse itself is tested: the minimum of q over the
-// box (zero if the centre is inside, else on an edge).  The margins (relative 1e-3 on the
-// bound, 1e-3 absolute, 1e-2 px on the box test) exceed the float32 error of the per-pixel
-// test, so a culled splat is one every pixel of the tile skips: culling changes no
-// decision of the forward or backward.
-__device__ __forceinline__ bool splat_touches_box(const float4 &r0, const float4 &r1, float bx0, float bx1,
-                                                  float by0, float by1)
-{
-    const float o = r1.y;
-    if (o * 255.0f < 0.9999f) return false;
-    const float A = r0.z, B = r0.w, C = r1.x;
-    const float det = A * C - B * B;
-    if (!(det > 0.f)) return true;
-    // alpha >= 1/255 needs q = A dx^2 + 2 B dx dy + C dy^2 <= 2 ln(255 o) (widened for rounding)
-    const float t2 = 2.0f * logf(255.0f * o) * 1.001f + 1e-3f;
-    const float u = r0.x, v = r0.y;
-    // the ellipse's bounding box against the box: a cheap first reject
-    const float ex = sqrtf(t2 * C / det) + 1e-2f, ey = sqrtf(t2 * A / det) + 1e-2f;
-    const float dx = fabsf(u - fminf(fmaxf(u, bx0), bx1));
-    const float dy = fabsf(v - fminf(fmaxf(v, by0), by1));
-    if (!(dx <= ex && dy <= ey)) return false;
-    if (dx == 0.f && dy == 0.f) return true;   // centre inside the box
-    // q is convex with its minimum at the centre, outside the box: its minimum over the box
-    // lies on an edge; along an edge q is a parabola, minimised at its clamped vertex
-    const float bc = B / C, ba = B / A;
-    float qmin = INFINITY;
-#pragma unroll
-    for (int e = 0; e < 2; e++) {
-        const float ddx = u - (e ? bx1 : bx0);
-        const float ddy = fminf(fmaxf(-bc * ddx, v - by1), v - by0);
-        qmin = fminf(qmin, fmaf(A * ddx, ddx, fmaf(2.f * B * ddx, ddy, C * ddy * ddy)));
-    }
-#pragma unroll
-    for (int e = 0; e < 2; e++) {
-        const float ddy = v - (e ? by1 : by0);
-        const float ddx = fminf(fmaxf(-ba * ddy, u - bx1), u - bx0);
-        qmin = fminf(qmin, fmaf(A * ddx, ddx, fmaf(2.f * B * ddx, ddy, C * ddy * ddy)));
-    }
-    return qmin <= t2;
-}
-
 // Exclusive prefix count of `keep` over the threads of the block (thread order) and the
 // block total; NW = warps per block.  Contains two barriers.
 template <int NW>
@@ -156,10 +110,10 @@ __host__ __device__ constexpr int min_blocks_for()
 // where tau = -ln(255 opacity): alpha = opacity exp(power) < 1/255 exactly when
 // power < tau, so both raster kernels test the exponent against tau and evaluate the
 // exponential only for pairs that can blend.
-__device__ __forceinline__ void stage_splat(const float4 &r0, const float4 &r1, float4 &t0, float4 &t1)
+__device__ __forceinline__ void stage_splat(const float4 &r0, const float4 &r1, float tau, float4 &t0, float4 &t1)
 {
     t0 = make_float4(r0.x, r0.y, -0.5f * r0.z, -r0.w);
-    t1 = make_float4(-0.5f * r1.x, r1.y, r1.z, -logf(255.0f * r1.y));
+    t1 = make_float4(-0.5f * r1.x, r1.y, r1.z, tau);
 }
 
 // Exponent of the projected Gaussian at a pixel from a staged splat, with explicit

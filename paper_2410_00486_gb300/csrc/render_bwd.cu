@@ -2,8 +2,8 @@
 //
 // One block per (view, tile), four vertically adjacent pixels per thread (two on 8x8
 // tiles), walking the tile's list back to front from the block's largest `last`.
-// Staging applies the forward's tile test and exponent threshold, so the same splats
-// are considered.  Each pixel recomputes alpha exactly as the forward did (same
+// A tile's list holds only splats that can reach alpha >= 1/255 in it (the binning's
+// test), the same list the forward walked.  Each pixel recomputes alpha exactly as the forward did (same
 // rounding, same decisions) and its transmittance from the stored final T,
 // T_j = T_{j+1} / (1 - alpha_j), so no per-pixel splat list is kept.
 //
@@ -76,7 +76,6 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
     __shared__ float4 s0[BD], s1[BD], s2[BD];
     __shared__ uint32_t sslot[BD], spos[BD];
     __shared__ uint32_t smax[NW];
-    __shared__ int wcnt[NW];
     int64_t tile;
     int view, tx, ty;
     item_tile(a.order, a.g, tile, view, tx, ty);
@@ -137,41 +136,24 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
     uint32_t maxlast = 0;
     for (int i = 0; i < NW; i++) maxlast = max(maxlast, smax[i]);
 
-    const float bx0 = (float)(tx * B), bx1 = (float)(min(tx * B + B, a.g.W) - 1);
-    const float by0 = (float)(ty * B), by1 = (float)(min(ty * B + B, a.g.H) - 1);
     for (int bend = (int)maxlast; bend > 0; bend -= BD) {
         const int bstart = max(0, bend - BD);
         const int nraw = bend - bstart;
         __syncthreads();
-        // stage positions [bstart, bend), keeping in list order only splats that can
-        // touch the tile (the forward applied the same test)
-        int cnt = 0;
+        // stage positions [bstart, bend) (every entry can reach the tile: the binning's test)
         for (int c0 = 0; c0 < BD; c0 += NT) {
             const int i = c0 + (int)threadIdx.x;
-            bool keep = false;
-            float4 r0, r1;
-            const float4 *r = nullptr;
-            uint32_t slot = 0;
-            if (i < nraw) {
-                slot = __ldg(a.vals + start + bstart + i);
-                r = a.rec + kRec4 * (size_t)slot;
-                r0 = __ldg(r);
-                r1 = __ldg(r + 1);
-                keep = splat_touches_box(r0, r1, bx0, bx1, by0, by1);
-            }
-            int tot;
-            const int pre = block_compact<NW>(keep, wcnt, tot);
-            if (keep) {
-                const int d = cnt + pre;
-                stage_splat(r0, r1, s0[d], s1[d]);
-                s2[d] = __ldg(r + 2);
-                sslot[d] = slot;
-                spos[d] = (uint32_t)(bstart + i);
-            }
-            cnt += tot;
+            if (i >= nraw) break;
+            const uint32_t slot = __ldg(a.vals + start + bstart + i);
+            const float4 *r = a.rec + kRec4 * (size_t)slot;
+            const float4 r2 = __ldg(r + 2);
+            stage_splat(__ldg(r), __ldg(r + 1), r2.w, s0[i], s1[i]);
+            s2[i] = r2;
+            sslot[i] = slot;
+            spos[i] = (uint32_t)(bstart + i);
         }
         __syncthreads();
-        for (int j = cnt - 1; j >= 0; j--) {
+        for (int j = nraw - 1; j >= 0; j--) {
             const uint32_t pos = spos[j];
             const float4 q0 = s0[j];
             const float4 q1 = s1[j];

@@ -131,9 +131,6 @@ k_render_bwd_splat(RasterBwdArgs a, const float4 *__restrict__ ck4, const float 
     for (int i = 0; i < kSplatWarps; i++) maxlast = max(maxlast, smax[i]);
     const int nbk = (int)((maxlast + kBucket - 1) / kBucket);
     const int64_t bbase = bucket_start[tile];
-    const float bx0 = (float)(tx * B), bx1 = (float)(min(tx * B + B, a.g.W) - 1);
-    const float by0 = (float)(ty * B), by1 = (float)(min(ty * B + B, a.g.H) - 1);
-
     for (int k = w; k < nbk; k += kSplatWarps) {
         const uint32_t pos = (uint32_t)(k * kBucket + lane);
         bool keep = false;
@@ -142,12 +139,9 @@ k_render_bwd_splat(RasterBwdArgs a, const float4 *__restrict__ ck4, const float 
         if (pos < maxlast) {
             slot = __ldg(a.vals + start + pos);
             const float4 *r = a.rec + kRec4 * (size_t)slot;
-            const float4 r0 = __ldg(r), r1 = __ldg(r + 1);
-            keep = splat_touches_box(r0, r1, bx0, bx1, by0, by1);
-            if (keep) {
-                stage_splat(r0, r1, q0, q1);
-                q2 = __ldg(r + 2);
-            }
+            keep = true;
+            q2 = __ldg(r + 2);
+            stage_splat(__ldg(r), __ldg(r + 1), q2.w, q0, q1);
         }
         if (__ballot_sync(kFull, keep) == 0u) continue;
         // this bucket's checkpoints (state before position 32 k) into the warp's slice

@@ -1,12 +1,10 @@
 // Forward blend of Eq. 1 (Sec. III-B, CaRtGS) with the L1 loss fused in.
 //
 // One block per (view, tile), two vertically adjacent pixels per thread.  The tile's
-// depth-sorted list is consumed in batches of BD splats: the block gathers the
-// records of a batch (48 bytes each, one per thread), drops splats whose
-// alpha >= 1/255 ellipse misses the tile (exact-safe, see splat_touches_box), and
-// compacts the survivors in list order into shared memory; every pixel then walks
-// the batch front to back, rejecting a pair on its exponent (power < tau) before any
-// exponential.  A block-wide vote (__syncthreads_count) ends the walk as soon as every
+// depth-sorted list (only splats that can reach alpha >= 1/255 in the tile: the binning's
+// test) is consumed in batches of BD splats: the block gathers the records of a batch
+// (48 bytes each, one per thread) into shared memory; every pixel then walks the batch
+// front to back, rejecting a pair on its exponent (power < tau) before any exponential.  A block-wide vote (__syncthreads_count) ends the walk as soon as every
 // pixel of the tile is saturated (T below 1e-4).
 #include "raster.cuh"
 
@@ -20,7 +18,6 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
     constexpr int NW = NT / 32;
     __shared__ float4 s0[BD], s1[BD], s2[BD];
     __shared__ uint32_t spos[BD];
-    __shared__ int wcnt[NW];
     __shared__ float red[5][NW];
     int64_t tile;
     int view, tx, ty;
@@ -30,8 +27,6 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
     const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
     const float fx = (float)px;
     // pixel-centre box of the tile (clipped to the image)
-    const float bx0 = (float)(tx * B), bx1 = (float)(min(tx * B + B, a.g.W) - 1);
-    const float by0 = (float)(ty * B), by1 = (float)(min(ty * B + B, a.g.H) - 1);
 
     float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
     uint32_t lst[PPT];
@@ -54,29 +49,16 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
     for (int p = 0; p < PPT; p++) active += done[p] ? 0u : 1u;
     for (uint32_t base = start; base < end; base += BD) {
         if (__syncthreads_count(!tdone) == 0) break;
-        // stage the batch, keeping (in list order) only splats that can touch the tile
-        int cnt = 0;
-        for (int c0 = 0; c0 < BD; c0 += NT) {
-            const int i = c0 + (int)threadIdx.x;
+        // stage the batch (every entry of a tile's list can reach the tile: the binning
+        // left out the rest)
+        const int cnt = (int)min((uint32_t)BD, end - base);
+        for (int i = threadIdx.x; i < cnt; i += NT) {
             const uint32_t idx = base + (uint32_t)i;
-            bool keep = false;
-            float4 r0, r1;
-            const float4 *r = nullptr;
-            if (i < BD && idx < end) {
-                r = a.rec + kRec4 * (size_t)__ldg(a.vals + idx);
-                r0 = __ldg(r);
-                r1 = __ldg(r + 1);
-                keep = splat_touches_box(r0, r1, bx0, bx1, by0, by1);
-            }
-            int tot;
-            const int pre = block_compact<NW>(keep, wcnt, tot);
-            if (keep) {
-                const int d = cnt + pre;
-                stage_splat(r0, r1, s0[d], s1[d]);
-                s2[d] = __ldg(r + 2);
-                spos[d] = idx - start;
-            }
-            cnt += tot;
+            const float4 *r = a.rec + kRec4 * (size_t)__ldg(a.vals + idx);
+            const float4 r2 = __ldg(r + 2);
+            stage_splat(__ldg(r), __ldg(r + 1), r2.w, s0[i], s1[i]);
+            s2[i] = r2;
+            spos[i] = idx - start;
         }
         __syncthreads();
         if (!tdone) {

@@ -113,7 +113,7 @@ class MappingWindow:
     def _alloc_capacity(self, cap: int):
         self.capacity = int(cap)
         self.vals = _u32(max(1, self.capacity), self.device)
-        ws = N.cgs_bin_sort_workspace(self.capacity, self.V, self.cfg)
+        ws = N.cgs_bin_sort_workspace(self.capacity, self.n, self.V, self.cfg)
         self.bin_ws = torch.empty(ws, dtype=torch.uint8, device=self.device)
         if self.backward_kind == "splat":
             # checkpoints of the splat-wise backward: at most capacity / 32 + tiles buckets
@@ -301,6 +301,7 @@ class MappingWindow:
         self.accum = torch.zeros(self.n, **f32)
         self.denom = torch.zeros(self.n, **f32)
         self.max_r2d = torch.zeros(self.n, **f32)
+        self._alloc_capacity(self.capacity)    # the binning workspace depends on n
         self._pv = None
         self.graph = None
 
@@ -313,7 +314,7 @@ class MappingWindow:
             pv["slot_grad"] = torch.zeros(n * N.REC_FLOATS, dtype=torch.float32, device=dev)
             pv["ranges"] = _u32(2 * self.Tv, dev)
             pv["order"] = _u32(self.Tv, dev) if self.order is not None else None
-            pv["ws"] = torch.empty(N.cgs_bin_sort_workspace(self.capacity, 1, self.cfg), dtype=torch.uint8,
+            pv["ws"] = torch.empty(N.cgs_bin_sort_workspace(self.capacity, n, 1, self.cfg), dtype=torch.uint8,
                                    device=dev)
             pv["fwd_ws"] = torch.empty(max(256, N.cgs_render_fwd_workspace(1, self.cfg)), dtype=torch.uint8,
                                        device=dev)

@@ -36,22 +36,24 @@ def native():
     return N
 
 
-def rec_to_gpu(rec10, radius, clamp):
+def rec_to_gpu(rec10, radius, tau=None):
+    """Library records (12 floats: u, v, A, B | C, o, z, radius | r, g, b, tau) from oracle
+    records; tau = -ln(255 o) rounded to float32 (O.tau32) unless given."""
     import torch
     m = rec10.shape[0]
     a = np.zeros((m, 12), np.float32)
     a[:, GPU_IDX] = rec10.astype(np.float32)
     a[:, 7] = np.ascontiguousarray(radius, np.int32).view(np.float32)
-    a[:, 11] = np.ascontiguousarray(clamp, np.int32).view(np.float32)
+    a[:, 11] = O.tau32(a[:, 5]) if tau is None else np.asarray(tau, np.float32)
     return torch.from_numpy(a.reshape(-1)).cuda()
 
 
 def rec_from_gpu(t):
+    """(oracle-order records [m, 10] in float64, radius int32 [m], tau float32 [m])."""
     a = t.detach().cpu().numpy().reshape(-1, 12)
     rec10 = a[:, GPU_IDX].astype(np.float64)
     radius = np.ascontiguousarray(a[:, 7]).view(np.int32).copy()
-    clamp = np.ascontiguousarray(a[:, 11]).view(np.int32).copy()
-    return rec10, radius, clamp
+    return rec10, radius, a[:, 11].copy()
 
 
 def sg_from_gpu(t):

@@ -43,7 +43,7 @@ def test_host_only_queries(native):
     assert native.cgs_param_count(300_000, 3) == 59 * 300_000
     assert native.cgs_param_count(10, 0) == 140
     assert native.cgs_tiles_per_view(cfg) == 75 * 43
-    assert native.cgs_bin_sort_workspace(1000, 16, cfg) > 16 * 75 * 43 * 8
+    assert native.cgs_bin_sort_workspace(1000, 300_000, 16, cfg) > 16 * 75 * 43 * 8
     bad = native.make_config(1200, 680, 12, 64, 3)
     assert native.cgs_tiles_per_view(bad) == -1
     assert native.status_string(-4).startswith("tile instance capacity")

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
-from synth import make_scene, make_tiny_scene, make_records
+from synth import make_conics, make_scene, make_tiny_scene, make_records
 from tests.gpu_util import (GRAD_REL_TOL, PIX_TOL, group_slices, native, oracle_targets, rec_from_gpu,
                             rec_to_gpu, rel_l2, round32, sg_from_gpu, sg_to_gpu, torch_cuda)
 
@@ -60,7 +60,7 @@ def test_preprocess_matches_oracle(name):
     sg = torch.full((V * n * 12,), 7.0, device="cuda")
     N.cgs_preprocess(params, n, cams, V, cfg, rec, sg)
     torch.cuda.synchronize()
-    g10, grad_r, gclamp = rec_from_gpu(rec)
+    g10, grad_r, gtau = rec_from_gpu(rec)
     ref = O.preprocess(sc.params, n, sc.sh_degree, sc.cams, sc.width, sc.height, sc.tile)
     fr = ref["fragile"] > 0
     vis_g, vis_o = grad_r > 0, ref["radius"] > 0
@@ -76,7 +76,9 @@ def test_preprocess_matches_oracle(name):
     assert e[:, 5].max() < 1e-6                                              # opacity
     assert e[:, 6:9].max() < 2e-5                                            # colour
     assert (e[:, 9] / r[:, 9]).max() < 1e-6                                  # depth
-    assert np.array_equal(gclamp[both], ref["clamp"][both])
+    # tau = -ln(255 o) of the record, as the float32 logarithm of the float32 opacity
+    tau_ref = -np.log(255.0 * ref["rec"][both, 5])
+    assert np.abs(gtau[both] - tau_ref).max() < 1e-5
     # slot gradients of visible slots are zeroed
     sga = sg.cpu().numpy().reshape(-1, 12)
     assert np.all(sga[vis_g] == 0.0)
@@ -89,7 +91,7 @@ def test_preprocess_matches_oracle(name):
 def gpu_bin(N, rec_gpu, n, V, cfg, capacity, order=True):
     torch = torch_cuda()
     Tv = N.cgs_tiles_per_view(cfg)
-    ws = torch.empty(N.cgs_bin_sort_workspace(capacity, V, cfg), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(N.cgs_bin_sort_workspace(capacity, n, V, cfg), dtype=torch.uint8, device="cuda")
     vals = torch.zeros(max(1, capacity), dtype=torch.int32, device="cuda")
     ranges = torch.zeros(2 * Tv * V, dtype=torch.int32, device="cuda")
     tord = torch.zeros(Tv * V, dtype=torch.int32, device="cuda") if order else None
@@ -117,11 +119,13 @@ def test_bin_sort_bit_exact(case):
     N = native()
     V, n, W, H, B, maxr = case
     u, v, r, z = make_records(17 + n, V, n, W, H, max_radius=maxr)
+    conic, opac = make_conics(18 + n, r)
     rec10 = np.zeros((V * n, 10))
     rec10[:, 0], rec10[:, 1], rec10[:, 9] = u, v, z
-    g = rec_to_gpu(rec10, r, np.zeros(V * n, np.int32))
+    rec10[:, 2:5], rec10[:, 5] = conic, opac
+    g = rec_to_gpu(rec10, r)
     cfg = N.make_config(W, H, B, 64, 0)
-    ranges_o, vals_o = O.bin_lists(u, v, z, r, V, n, W, H, B)
+    ranges_o, vals_o = O.bin_lists(u, v, z, r, V, n, W, H, B, conic=conic, tau=O.tau32(opac))
     cnt = len(vals_o)
     vals, ranges, tord, ninst, st = gpu_bin(N, g, n, V, cfg, cnt + 7)
     assert st == 0 and ninst == cnt
@@ -142,11 +146,13 @@ def test_bin_sort_capacity_overflow_reports_and_truncates():
     N = native()
     V, n, W, H, B = 2, 3000, 200, 150, 16
     u, v, r, z = make_records(5, V, n, W, H, max_radius=25)
+    conic, opac = make_conics(6, r)
     rec10 = np.zeros((V * n, 10))
     rec10[:, 0], rec10[:, 1], rec10[:, 9] = u, v, z
-    g = rec_to_gpu(rec10, r, np.zeros(V * n, np.int32))
+    rec10[:, 2:5], rec10[:, 5] = conic, opac
+    g = rec_to_gpu(rec10, r)
     cfg = N.make_config(W, H, B, 64, 0)
-    _, vals_o = O.bin_lists(u, v, z, r, V, n, W, H, B)
+    _, vals_o = O.bin_lists(u, v, z, r, V, n, W, H, B, conic=conic, tau=O.tau32(opac))
     cap = len(vals_o) // 3
     vals, ranges, _, ninst, st = gpu_bin(N, g, n, V, cfg, cap)
     assert st == N.CGS_ERR_CAPACITY
@@ -162,7 +168,7 @@ def test_bin_sort_empty_and_all_culled():
     cfg = N.make_config(64, 48, 16, 64, 0)
     rec10 = np.zeros((V * n, 10))
     rec10[:, 9] = 1.0
-    g = rec_to_gpu(rec10, np.zeros(V * n, np.int32), np.zeros(V * n, np.int32))
+    g = rec_to_gpu(rec10, np.zeros(V * n, np.int32))
     vals, ranges, tord, ninst, st = gpu_bin(N, g, n, V, cfg, 16)
     assert st == 0 and ninst == 0
     assert not ranges.cpu().numpy().any()
@@ -176,8 +182,7 @@ def stage_inputs(name, bg=(0.0, 0.0, 0.0)):
     V, n = sc.views, sc.n
     pre = O.preprocess(sc.params, n, sc.sh_degree, sc.cams, sc.width, sc.height, sc.tile)
     rec = round32(pre["rec"])
-    ranges, vals = O.bin_lists(rec[:, 0], rec[:, 1], rec[:, 9], pre["radius"], V, n, sc.width, sc.height,
-                               sc.tile)
+    ranges, vals = O.bin_records(rec, pre["radius"], V, n, sc.width, sc.height, sc.tile)
     fw = O.render_fwd(rec, ranges, vals, V, sc.width, sc.height, sc.tile, sc.cams, bg, tgt_rgb, tgt_d, 0.1,
                       tol=1e-5)
     return sc, tgt_rgb, tgt_d, pre, rec, ranges, vals, fw
@@ -188,7 +193,7 @@ def gpu_forward_from_rec(N, sc, rec, pre, tgt_rgb, tgt_d, batch_depth=64, bg=(0.
     torch = torch_cuda()
     V, n, H, W = sc.views, sc.n, sc.height, sc.width
     cfg = cfg_for(N, sc, batch_depth, bg=bg)
-    g = rec_to_gpu(rec, pre["radius"], pre["clamp"])
+    g = rec_to_gpu(rec, pre["radius"])
     vals, ranges, tord, ninst, st = gpu_bin(N, g, n, V, cfg, cap, order)
     assert st == 0
     out = dict(rec=g, vals=vals, ranges=ranges, order=tord, cfg=cfg)
@@ -242,8 +247,7 @@ def test_render_fwd_background_and_ragged_tiles():
     sc, tgt_rgb, tgt_d = scene("tiny_sh3_3views")   # 52x37 with 8x8 tiles: ragged in x and y
     pre = O.preprocess(sc.params, sc.n, 3, sc.cams, sc.width, sc.height, sc.tile)
     rec = round32(pre["rec"])
-    ranges, vals = O.bin_lists(rec[:, 0], rec[:, 1], rec[:, 9], pre["radius"], sc.views, sc.n, sc.width,
-                               sc.height, sc.tile)
+    ranges, vals = O.bin_records(rec, pre["radius"], sc.views, sc.n, sc.width, sc.height, sc.tile)
     fw = O.render_fwd(rec, ranges, vals, sc.views, sc.width, sc.height, sc.tile, sc.cams, bg, tgt_rgb, tgt_d,
                       0.1, tol=1e-5)
     out = gpu_forward_from_rec(N, sc, rec, pre, tgt_rgb, tgt_d, 32, bg=bg, order=False)
@@ -437,7 +441,7 @@ def test_densify_stats_kernel_matches_oracle():
     V, n = 4, 5000
     radius = rng.integers(0, 30, V * n).astype(np.int32)
     rec10 = np.zeros((V * n, 10))
-    g = rec_to_gpu(rec10, radius, np.zeros(V * n, np.int32))
+    g = rec_to_gpu(rec10, radius, np.zeros(V * n, np.float32))
     sg = np.zeros((V * n, 10))
     sg[:, :2] = rng.normal(0, 1e-4, (V * n, 2))
     sgg = sg_to_gpu(sg)
@@ -547,12 +551,12 @@ def test_splat_backward_matches_oracle(name, bd, tile):
     V, n, H, W = sc.views, sc.n, sc.height, sc.width
     pre = O.preprocess(sc.params, n, sc.sh_degree, sc.cams, W, H, tile)
     rec = round32(pre["rec"])
-    ranges, vals = O.bin_lists(rec[:, 0], rec[:, 1], rec[:, 9], pre["radius"], V, n, W, H, tile)
+    ranges, vals = O.bin_records(rec, pre["radius"], V, n, W, H, tile)
     fw = O.render_fwd(rec, ranges, vals, V, W, H, tile, sc.cams, (0.0, 0.0, 0.0), tgt_rgb, tgt_d, 0.1, tol=1e-5)
     ref = O.render_bwd(rec, ranges, vals, V, n, W, H, tile, sc.cams, fw["img"], fw["depth"], tgt_rgb, tgt_d,
                        fw["depth_count"])
     cfg = N.make_config(W, H, tile, bd, sc.sh_degree, 0.2, (0.0, 0.0, 0.0), 0.1)
-    g = rec_to_gpu(rec, pre["radius"], pre["clamp"])
+    g = rec_to_gpu(rec, pre["radius"])
     cap = len(vals) + 16
     gv, gr, go, ninst, st = gpu_bin(N, g, n, V, cfg, cap)
     assert st == 0

@@ -20,7 +20,7 @@ def _setup(N, torch, sc, seed):
     N.cgs_preprocess(params, n, cams, V, cfg, rec, None)
     cap = 1 << 23
     Tv = N.cgs_tiles_per_view(cfg)
-    ws = torch.empty(N.cgs_bin_sort_workspace(cap, V, cfg), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(N.cgs_bin_sort_workspace(cap, n, V, cfg), dtype=torch.uint8, device="cuda")
     vals = torch.zeros(cap, dtype=torch.int32, device="cuda")
     ranges = torch.zeros(2 * Tv * V, dtype=torch.int32, device="cuda")
     order = torch.zeros(Tv * V, dtype=torch.int32, device="cuda")
