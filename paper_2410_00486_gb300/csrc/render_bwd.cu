@@ -3,8 +3,8 @@
 // One block per (view, tile), four vertically adjacent pixels per thread (two on 8x8
 // tiles), walking the tile's list back to front from the block's largest `last`.
 // A tile's list holds only splats that can reach alpha >= 1/255 in it (the binning's
-// test), the same list the forward walked.  Each pixel recomputes alpha exactly as the forward did (same
-// rounding, same decisions) and its transmittance from the stored final T,
+// test), the same list the forward walked.  Each pixel recomputes alpha exactly as the
+// forward did (same rounding, same decisions) and its transmittance from the stored final T,
 // T_j = T_{j+1} / (1 - alpha_j), so no per-pixel splat list is kept.
 //
 // With R_j the colour behind splat j normalised by the transmittance just after it,
@@ -14,58 +14,27 @@
 // recursion with c_j . gI + z_j gD in place of the colour.
 //
 // The per-(splat, pixel) gradients of a thread's pixels are added in registers (the
-// pixels share dx, so the dx moments are formed once per thread), then a warp's pixels
-// are summed with a butterfly reduce-scatter (15 shuffles for 10 fields instead of 50
-// for a plain tree per field), after which ten lanes each issue one atomic add into
-// the slot's gradient record; when only a few lanes contributed they add their own sums
-// directly instead.  Warps where no pixel blended the splat skip it (vote).
+// pixels share dx, so the dx moments are formed once per thread), then a warp's rows of
+// ten sums are added through shared memory (each lane stores its row, thirty lanes add
+// one field over a third of the rows each, two shuffles join the thirds), after which
+// ten lanes each issue one atomic add into the slot's gradient record; when only a few
+// lanes contributed they add their own sums directly instead.  Warps where no pixel
+// blended the splat skip it (vote).
 #include "raster.cuh"
 
 namespace cgs {
 
 // Splats to which at most this many lanes of a warp contribute are added with per-lane
-// atomics (L2 reductions); more contributors go through the warp reduce-scatter.  Measured
-// on the 16-view window: 1 lane 5.81 ms, 8 lanes 5.62, 12-16 lanes 5.55, 24 lanes 5.97,
-// and every lane direct 25.9 (same-address atomics serialise).
+// atomics (L2 reductions); more contributors go through the warp sum.  Measured on the
+// 16-view window (raster backward ms): 4 lanes 5.02, 8 lanes 4.92, 12 lanes 4.88,
+// 16 lanes 4.91; every lane direct is five times slower (same-address atomics serialise).
 constexpr int kDirectLanes = 12;
 
-__device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
+// Row stride (floats) of the per-warp reduction buffer: ten fields padded to 12.
+constexpr int kRedStride = 12;
+constexpr int kRedRows = 33;   // 32 lanes and a zero row
 
-// Reduce-scatter of 16 per-lane values over the warp.  On return lane l holds the
-// warp sum of value index ((l>>4)&1)*8 + ((l>>3)&1)*4 + ((l>>2)&1)*2 + ((l>>1)&1).
-// Value 7 and values 11..15 are always zero here; the pair (7, 15) needs no shuffle.
-__device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane)
-{
-    const bool b4 = lane & 16;
-#pragma unroll
-    for (int i = 0; i < 7; i++) {
-        const float mine = b4 ? v[i + 8] : v[i];
-        const float other = b4 ? v[i] : v[i + 8];
-        v[i] = mine + __shfl_xor_sync(kFull, other, 16);
-    }
-    v[7] = 0.f;
-    const bool b3 = lane & 8;
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        const float mine = b3 ? v[i + 4] : v[i];
-        const float other = b3 ? v[i] : v[i + 4];
-        v[i] = mine + __shfl_xor_sync(kFull, other, 8);
-    }
-    const bool b2 = lane & 4;
-#pragma unroll
-    for (int i = 0; i < 2; i++) {
-        const float mine = b2 ? v[i + 2] : v[i];
-        const float other = b2 ? v[i] : v[i + 2];
-        v[i] = mine + __shfl_xor_sync(kFull, other, 4);
-    }
-    const bool b1 = lane & 2;
-    {
-        const float mine = b1 ? v[1] : v[0];
-        const float other = b1 ? v[0] : v[1];
-        v[0] = mine + __shfl_xor_sync(kFull, other, 2);
-    }
-    return v[0] + __shfl_xor_sync(kFull, v[0], 1);
-}
+__device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
 
 template <int B, int BD>
 __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<B, kPPTBwd, kBwdMinWarps>())) k_render_bwd(RasterBwdArgs a)
@@ -76,6 +45,10 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
     __shared__ float4 s0[BD], s1[BD], s2[BD];
     __shared__ uint32_t sslot[BD], spos[BD];
     __shared__ uint32_t smax[NW];
+    __shared__ __align__(16) float red[NW * 2 * kRedRows * kRedStride];   // per warp, double-buffered
+    int rbuf = 0;
+    for (int i = threadIdx.x; i < NW * 2 * kRedStride; i += NT)   // the zero row of every buffer
+        red[(i / kRedStride) * (kRedRows * kRedStride) + 32 * kRedStride + i % kRedStride] = 0.f;
     int64_t tile;
     int view, tx, ty;
     item_tile(a.order, a.g, tile, view, tx, ty);
@@ -220,24 +193,31 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
                 continue;
             }
             {
-                float v[16];
-                v[0] = m0;
-                v[1] = sdpy;
-                v[2] = m0 * dx;
-                v[3] = m3;
-                v[4] = sdpyy;
-                v[5] = go;
-                v[6] = gz;
-                v[7] = 0.f;
-                v[8] = gr;
-                v[9] = gg;
-                v[10] = gb;
+                // warp sum of the ten fields through shared memory: every lane stores its
+                // row, then lanes 10g + f (g < 3, f < 10) add field f over rows g, g + 3,
+                // g + 6, ... and three shuffles combine the groups (row stride 12 floats:
+                // the 16-byte stores are conflict-free, the column reads nearly so)
+                float *buf = red + (size_t)((threadIdx.x >> 5) * 2 + rbuf) * (kRedRows * kRedStride);
+                rbuf ^= 1;
+                float4 *row = reinterpret_cast<float4 *>(buf + lane * kRedStride);
+                row[0] = make_float4(m0, sdpy, m0 * dx, m3);
+                row[1] = make_float4(sdpyy, go, gz, gr);
+                row[2] = make_float4(gg, gb, 0.f, 0.f);
+                __syncwarp();
+                const int g = lane / 10, f = lane - 10 * g;
+                float sum = 0.f;
+                if (lane < 30) {
+                    // rows g, g + 3, ..., g + 30; row 32 (group 2's last) is a zero row
+                    const float *col = buf + g * kRedStride + f;
 #pragma unroll
-                for (int k = 11; k < 16; k++) v[k] = 0.f;
-                float sum = warp_reduce_scatter16(v, lane);
-                const int f = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-                // fields 0 and 1 sit in lanes that differ in bit 1: exchange the two first moments
-                const float other = __shfl_xor_sync(kFull, sum, 2);
+                    for (int k = 0; k < 11; k++) sum += col[3 * k * kRedStride];
+                }
+                {
+                    const float p1 = __shfl_down_sync(kFull, sum, 10), p2 = __shfl_down_sync(kFull, sum, 20);
+                    sum += p1 + p2;   // lanes 0..9: field sums (groups 0, 1, 2)
+                }
+                // fields 0 and 1 (first moments) sit in lanes 0 and 1: exchange them
+                const float other = __shfl_xor_sync(kFull, sum, 1);
                 // power = -(A dx^2 + C dy^2)/2 - B dx dy with dx = u - x:
                 //   dL/du = -(A S_dx + B S_dy), dL/dv = -(C S_dy + B S_dx),
                 //   dL/dA = -S_xx / 2, dL/dB = -S_xy, dL/dC = -S_yy / 2
@@ -247,7 +227,8 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
                 else if (f == 1) sum = 2.f * hC * sum + q0.w * other;
                 else if (f == 2 || f == 4) sum = -0.5f * sum;
                 else if (f == 3) sum = -sum;
-                if (!(lane & 1) && f != 7 && f < 11) atomicAdd(a.sgrad + (size_t)sslot[j] * 12 + f, sum);
+                // record fields 0..6 (u, v, A, B, C, o, z), 8..10 (r, g, b)
+                if (lane < 10) atomicAdd(a.sgrad + (size_t)sslot[j] * 12 + (f < 7 ? f : f + 1), sum);
             }
         }
     }

@@ -82,7 +82,6 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
                 const float4 q0 = s0[j];
                 const float4 q1 = s1[j];
                 const PowerX pxs = power_x(q0, __fsub_rn(q0.x, fx));
-                n_eval += active;
 #pragma unroll
                 for (int p = 0; p < PPT; p++) {
                     if (done[p]) continue;
@@ -93,6 +92,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
                     if (testT < kTMin) {
                         done[p] = true;
                         active--;
+                        n_eval += spos[j] + 1u;    // work count: list entries this pixel evaluated
                         continue;
                     }
                     const float wgt = __fmul_rn(alpha, T[p]);
@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
         }
     }
 
+    n_eval += active * (end - start);   // pixels that never stopped evaluated the whole list
     float l_rgb = 0.f, l_d = 0.f, c_d = 0.f;
     const size_t HW = (size_t)a.g.W * a.g.H;
 #pragma unroll
