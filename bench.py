@@ -525,7 +525,14 @@ def stage_breakdown(win, N, reps=5):
         torch.cuda.synchronize()
         for i, k in enumerate(names):
             acc[k] += ev[i].elapsed_time(ev[i + 1]) / reps
-    # work counts of this window (measurement only)
+    # work counts of this window (measurement only): one more forward over the same records
+    # and lists with the blended-pair counter compiled in (the timed forward leaves it out)
+    cc = type(c).from_buffer_copy(c)
+    cc.count_work = 1
+    N.cgs_render_fwd(win.rec, win.vals, win.ranges, win.order, win.V, cc, win.view_weight, win.tgt_rgb,
+                     win.tgt_depth, win.img, win.depth, win.t_final, win.last, win.loss_view,
+                     win.depth_count, win.fwd_ws, win.status)
+    torch.cuda.synchronize()
     part = win.fwd_ws[: 4 * 5 * win.Ttot].view(torch.float32).view(win.Ttot, 5).double()
     rad = win.rec.view(torch.int32).view(-1, 12)[:, 7]
     work = {

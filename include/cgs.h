@@ -83,6 +83,9 @@ typedef struct {
     float lambda_depth;      /* weight of the masked depth L1 term (0.1) */
     int32_t batch_depth_bwd; /* splats per batch in the pixel-wise raster backward: 0 (same as
                                 batch_depth), 32, 64, 128 or 256 */
+    int32_t count_work;      /* nonzero: cgs_render_fwd also counts the (splat, pixel) pairs it
+                                blends (per-tile partial 4; a per-pair counter, about 5% of the
+                                blend's time); 0: that partial is written as 0 */
 } cgs_config;
 
 /* Number of floats in the parameter vector: (14 + 3 (K-1)) n. */
@@ -170,7 +173,8 @@ int cgs_bin_sort(const float *rec, int64_t n, int32_t V, const cgs_config *cfg, 
  *   workspace     device scratch of cgs_render_fwd_workspace(V, cfg) bytes (required); on
  *                 return it holds float[V * tiles_per_view][5] per-tile partial sums: sum |r_rgb|,
  *                 sum |r_depth| over valid depth pixels, valid depth count, (splat, pixel)
- *                 pairs evaluated, pairs blended (the last two are the blend's work counts)
+ *                 pairs evaluated, pairs blended (the last two are the blend's work counts;
+ *                 pairs blended only with cfg->count_work, else 0)
  */
 size_t cgs_render_fwd_workspace(int32_t V, const cgs_config *cfg);
 int cgs_render_fwd(const float *rec, const uint32_t *vals, const uint32_t *ranges,

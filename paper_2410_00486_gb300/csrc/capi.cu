@@ -162,6 +162,7 @@ int cgs_render_fwd(const float *rec, const uint32_t *vals, const uint32_t *range
     a.ckD = nullptr;
     a.bucket_start = nullptr;
     a.max_buckets = 0;
+    a.count_blend = cfg->count_work != 0;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = raster_fwd(a, cfg->tile, cfg->batch_depth, s);
     if (e == cudaSuccess && tgt_rgb)

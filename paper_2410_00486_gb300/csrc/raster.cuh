@@ -21,6 +21,7 @@ struct RasterFwdArgs {
     float *ckD;                  // [bucket][B*B] depth
     const uint32_t *bucket_start;  // [Ttot + 1] first bucket of each tile
     int64_t max_buckets;
+    bool count_blend;              // count blended pairs (partial 4); else it is written as 0
 };
 
 // Checkpoint bucket of list positions [32 k, 32 k + 32) of a tile.

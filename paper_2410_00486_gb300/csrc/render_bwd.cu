@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
     constexpr int NT = B * B / PPT;
     constexpr int NW = NT / 32;
     __shared__ float4 s0[BD], s1[BD], s2[BD];
-    __shared__ uint32_t sslot[BD], spos[BD];
+    __shared__ uint32_t sslot[BD];
     __shared__ uint32_t smax[NW];
     __shared__ __align__(16) float red[NW * 2 * kRedRows * kRedStride];   // per warp, double-buffered
     int rbuf = 0;
@@ -123,11 +123,10 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
             stage_splat(__ldg(r), __ldg(r + 1), r2.w, s0[i], s1[i]);
             s2[i] = r2;
             sslot[i] = slot;
-            spos[i] = (uint32_t)(bstart + i);
         }
         __syncthreads();
         for (int j = nraw - 1; j >= 0; j--) {
-            const uint32_t pos = spos[j];
+            const uint32_t pos = (uint32_t)(bstart + j);   // list position of splat j
             const float4 q0 = s0[j];
             const float4 q1 = s1[j];
             const float dx = __fsub_rn(q0.x, fx);

@@ -312,6 +312,7 @@ int cgs_render_fwd_ckpt(const float *rec, const uint32_t *vals, const uint32_t *
     a.ckD = ckpt + 4 * (size_t)max_buckets * cfg->tile * cfg->tile;
     a.bucket_start = bucket_start;
     a.max_buckets = max_buckets;
+    a.count_blend = cfg->count_work != 0;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = raster_fwd(a, cfg->tile, cfg->batch_depth, s);
     if (e == cudaSuccess && tgt_rgb)

@@ -10,14 +10,13 @@
 
 namespace cgs {
 
-template <int B, int BD, bool CKPT>
+template <int B, int BD, bool CKPT, bool COUNT>
 __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<B, kPPTFwd, kFwdMinWarps>())) k_render_fwd(RasterFwdArgs a)
 {
     constexpr int PPT = ppt_for<B, kPPTFwd>();
     constexpr int NT = B * B / PPT;
     constexpr int NW = NT / 32;
     __shared__ float4 s0[BD], s1[BD], s2[BD];
-    __shared__ uint32_t spos[BD];
     __shared__ float red[5][NW];
     int64_t tile;
     int view, tx, ty;
@@ -58,15 +57,14 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
             const float4 r2 = __ldg(r + 2);
             stage_splat(__ldg(r), __ldg(r + 1), r2.w, s0[i], s1[i]);
             s2[i] = r2;
-            spos[i] = idx - start;
         }
         __syncthreads();
         if (!tdone) {
             for (int j = 0; j < cnt; j++) {
+                const uint32_t pos = base - start + (uint32_t)j;   // list position of splat j
                 if (CKPT) {
                     // save the state of this thread's pixels at every boundary up to this splat
-                    const uint32_t sp = spos[j];
-                    while (next_ck <= sp) {
+                    while (next_ck <= pos) {
                         const int64_t bk = ck_base + (int64_t)(next_ck / kBucket);
                         if (bk < a.max_buckets) {
 #pragma unroll
@@ -92,7 +90,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
                     if (testT < kTMin) {
                         done[p] = true;
                         active--;
-                        n_eval += spos[j] + 1u;    // work count: list entries this pixel evaluated
+                        n_eval += pos + 1u;    // work count: list entries this pixel evaluated
                         continue;
                     }
                     const float wgt = __fmul_rn(alpha, T[p]);
@@ -102,8 +100,8 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
                     C2[p] = fmaf(q2.z, wgt, C2[p]);
                     D[p] = fmaf(q1.z, wgt, D[p]);
                     T[p] = testT;
-                    lst[p] = spos[j] + 1u;
-                    n_blend++;
+                    lst[p] = pos + 1u;
+                    if (COUNT) n_blend++;
                 }
                 if (active == 0u) break;
             }
@@ -209,10 +207,13 @@ template <int B, int BD>
 static cudaError_t launch_fwd(const RasterFwdArgs &a, cudaStream_t s)
 {
     const int64_t items = a.g.Tv * a.V;
-    if (a.ck4)
-        k_render_fwd<B, BD, true><<<(unsigned)items, B * B / ppt_for<B, kPPTFwd>(), 0, s>>>(a);
+    const int nt = B * B / ppt_for<B, kPPTFwd>();
+    if (a.ck4)   // the checkpointing forward does not count blended pairs
+        k_render_fwd<B, BD, true, false><<<(unsigned)items, nt, 0, s>>>(a);
+    else if (a.count_blend)
+        k_render_fwd<B, BD, false, true><<<(unsigned)items, nt, 0, s>>>(a);
     else
-        k_render_fwd<B, BD, false><<<(unsigned)items, B * B / ppt_for<B, kPPTFwd>(), 0, s>>>(a);
+        k_render_fwd<B, BD, false, false><<<(unsigned)items, nt, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -332,6 +333,7 @@ extern "C" int cgs_render_fwd_noalloc(const float *rec, const uint32_t *vals, co
     a.ckD = nullptr;
     a.bucket_start = nullptr;
     a.max_buckets = 0;
+    a.count_blend = cfg->count_work != 0;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = raster_fwd(a, cfg->tile, cfg->batch_depth, s);
     if (e == cudaSuccess && tgt_rgb)

@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(native):
 
 def test_struct_sizes_match_header(native):
     assert ctypes.sizeof(native.cgs_camera) == 80
-    assert ctypes.sizeof(native.cgs_config) == 4 * 11
+    assert ctypes.sizeof(native.cgs_config) == 4 * 12
 
 
 def test_host_only_queries(native):
