@@ -137,10 +137,9 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
             bool contrib = false;
 #pragma unroll
             for (int p = 0; p < PPT; p++) {
-                if (!(pos < lst[p])) continue;
                 const float dy = __fsub_rn(q0.y, fy0 + (float)p);
                 const float power = power_at(pxs, q1.x, dy);
-                if (power > 0.f || power < q1.w) continue;
+                if (!(pos < lst[p]) || power > 0.f || power < q1.w) continue;
                 const float G = __expf(power);
                 const float araw = __fmul_rn(q1.y, G);
                 const float alpha = fminf(kAlphaMax, araw);

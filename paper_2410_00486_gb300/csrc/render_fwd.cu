@@ -10,6 +10,10 @@
 
 namespace cgs {
 
+// Row coordinate of a finished pixel (outside the image, or saturated): a quiet NaN, so
+// its exponent is NaN and it fails the alpha test with no branch of its own.
+__device__ constexpr float kNoRow = __builtin_nanf("");
+
 template <int B, int BD, bool CKPT, bool COUNT>
 __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<B, kPPTFwd, kFwdMinWarps>())) k_render_fwd(RasterFwdArgs a)
 {
@@ -38,6 +42,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
         C0[p] = C1[p] = C2[p] = D[p] = 0.f;
         lst[p] = 0;
         done[p] = !(px < a.g.W && py0 + p < a.g.H);
+        if (done[p]) fy[p] = kNoRow;
         tdone = tdone && done[p];
     }
     uint32_t n_eval = 0, n_blend = 0, active = 0;
@@ -82,15 +87,17 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
                 const PowerX pxs = power_x(q0, __fsub_rn(q0.x, fx));
 #pragma unroll
                 for (int p = 0; p < PPT; p++) {
-                    if (done[p]) continue;
                     const float power = power_at(pxs, q1.x, __fsub_rn(q0.y, fy[p]));
-                    if (power > 0.f || power < q1.w) continue;
+                    // the alpha >= 1/255 test; a finished pixel (row NaN, so power NaN) fails it
+                    if (!(power <= 0.f && power >= q1.w)) continue;
                     const float alpha = fminf(kAlphaMax, __fmul_rn(q1.y, __expf(power)));
                     const float testT = __fmul_rn(T[p], __fsub_rn(1.f, alpha));
                     if (testT < kTMin) {
                         done[p] = true;
+                        fy[p] = kNoRow;
                         active--;
                         n_eval += pos + 1u;    // work count: list entries this pixel evaluated
+                        if (active == 0u) goto walked;   // every pixel of the thread is finished
                         continue;
                     }
                     const float wgt = __fmul_rn(alpha, T[p]);
@@ -103,8 +110,8 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
                     lst[p] = pos + 1u;
                     if (COUNT) n_blend++;
                 }
-                if (active == 0u) break;
             }
+        walked:
             tdone = true;
 #pragma unroll
             for (int p = 0; p < PPT; p++) tdone = tdone && done[p];
