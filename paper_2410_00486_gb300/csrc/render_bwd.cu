@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
             const uint32_t pos = (uint32_t)(bstart + j);   // list position of splat j
             const float4 q0 = s0[j];
             const float4 q1 = s1[j];
+            const float4 q2 = s2[j];
             const float dx = __fsub_rn(q0.x, fx);
             const PowerX pxs = power_x(q0, dx);
             // per-thread sums over its pixels: colour / depth / opacity gradients, and the
@@ -144,7 +145,6 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
                 const float araw = __fmul_rn(q1.y, G);
                 const float alpha = fminf(kAlphaMax, araw);
                 contrib = true;
-                const float4 q2 = s2[j];
                 const float inv_om = __fdividef(1.f, __fsub_rn(1.f, alpha));
                 T[p] = T[p] * inv_om;                             // transmittance before splat j
                 const float wT = alpha * T[p];

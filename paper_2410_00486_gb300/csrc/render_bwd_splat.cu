@@ -218,7 +218,7 @@ k_render_bwd_splat(RasterBwdArgs a, const float4 *__restrict__ ck4, const float 
             C1 = n1;
             C2 = n2;
             D = nD;
-            T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+            T = __fsub_rn(T, wT);   // T (1 - alpha), rounded as the forward does
         }
         if (keep) {
             float *gp = a.sgrad + (size_t)slot * 12;

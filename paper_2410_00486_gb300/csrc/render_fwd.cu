@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
                 }
                 const float4 q0 = s0[j];
                 const float4 q1 = s1[j];
+                const float4 q2 = s2[j];
                 const PowerX pxs = power_x(q0, __fsub_rn(q0.x, fx));
 #pragma unroll
                 for (int p = 0; p < PPT; p++) {
@@ -91,7 +92,8 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
                     // the alpha >= 1/255 test; a finished pixel (row NaN, so power NaN) fails it
                     if (!(power <= 0.f && power >= q1.w)) continue;
                     const float alpha = fminf(kAlphaMax, __fmul_rn(q1.y, __expf(power)));
-                    const float testT = __fmul_rn(T[p], __fsub_rn(1.f, alpha));
+                    const float wgt = __fmul_rn(alpha, T[p]);
+                    const float testT = __fsub_rn(T[p], wgt);   // T (1 - alpha)
                     if (testT < kTMin) {
                         done[p] = true;
                         fy[p] = kNoRow;
@@ -100,8 +102,6 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
                         if (active == 0u) goto walked;   // every pixel of the thread is finished
                         continue;
                     }
-                    const float wgt = __fmul_rn(alpha, T[p]);
-                    const float4 q2 = s2[j];
                     C0[p] = fmaf(q2.x, wgt, C0[p]);
                     C1[p] = fmaf(q2.y, wgt, C1[p]);
                     C2[p] = fmaf(q2.z, wgt, C2[p]);
