@@ -362,6 +362,7 @@ __device__ __forceinline__ uint32_t next_pow2(uint32_t x)
 // per-warp digit histograms scanned digit-major give each (digit, warp) its start.
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kTieRun = 32;   // longest run of equal 16-bit depth prefixes fixed by insertion
 
 // Lanes of the warp whose 8-bit digit equals this lane's (restricted to `valid` lanes),
 // from eight ballots, one per digit bit (a ballot-based multisplit: __match_any_sync
@@ -402,7 +403,8 @@ k_sort_tiles(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ k
     __shared__ uint64_t bufA[kSmallCap], bufB[kSmallCap];
     __shared__ uint32_t hist[kRsWarps][256];
     __shared__ uint16_t lrank[kSmallCap];
-    __shared__ uint32_t wsum[kRsWarps], wor[kRsWarps], wand[kRsWarps];
+    __shared__ uint32_t wsum[kRsWarps], wmin[kRsWarps], wmax[kRsWarps];
+    __shared__ int s_long;   // a run of equal 16-bit prefixes longer than kTieRun
     const int64_t t = blockIdx.x;
     const uint32_t st = ranges[2 * t], en = ranges[2 * t + 1];
     const uint32_t len = en - st;
@@ -416,98 +418,123 @@ k_sort_tiles(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ k
         return;
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // load, and find the depth bits that vary across the tile
-    uint32_t bor = 0u, band = ~0u;
+    // load, and find the range of the depth bits over the tile (positive floats: the bits
+    // order like the values)
+    uint32_t dmin = ~0u, dmax = 0u;
     for (uint32_t i = threadIdx.x; i < len; i += kRsThreads) {
         const uint64_t k = keys[st + i];
         bufA[i] = k;
         const uint32_t d = (uint32_t)(k >> 32);
-        bor |= d;
-        band &= d;
+        dmin = min(dmin, d);
+        dmax = max(dmax, d);
     }
     for (int off = 16; off > 0; off >>= 1) {
-        bor |= __shfl_xor_sync(kFull, bor, off);
-        band &= __shfl_xor_sync(kFull, band, off);
+        dmin = min(dmin, __shfl_xor_sync(kFull, dmin, off));
+        dmax = max(dmax, __shfl_xor_sync(kFull, dmax, off));
     }
     if (lane == 0) {
-        wor[w] = bor;
-        wand[w] = band;
+        wmin[w] = dmin;
+        wmax[w] = dmax;
     }
+    if (threadIdx.x == 0) s_long = 0;
     __syncthreads();
-    uint32_t vary = 0u, all_and = ~0u;
+    dmin = ~0u;
+    dmax = 0u;
     for (int i = 0; i < kRsWarps; i++) {
-        vary |= wor[i];
-        all_and &= wand[i];
+        dmin = min(dmin, wmin[i]);
+        dmax = max(dmax, wmax[i]);
     }
-    vary ^= all_and;
     uint64_t *src = bufA, *dst = bufB;
     const uint32_t per = (len + kRsWarps - 1) / kRsWarps;
     const uint32_t seg0 = min(len, (uint32_t)w * per), seg1 = min(len, seg0 + per);
-    for (int shift = 0; shift < 32; shift += 8) {
-        if (((vary >> shift) & 0xffu) == 0u) continue;      // block-uniform
-        for (int i = lane; i < 256; i += 32) hist[w][i] = 0u;
-        __syncwarp();
-        // count, and keep each key's rank among the equal digits of this warp's segment
-        // (earlier 32-key groups first, then lanes in order): the scatter below needs no
-        // ranking of its own
-        for (uint32_t c = seg0; c < seg1; c += 32) {
-            const uint32_t e = c + lane;
-            const bool valid = e < seg1;
-            const uint32_t d = valid ? ((uint32_t)(src[e] >> (32 + shift)) & 0xffu) : 0u;
-            const unsigned peers = same_digit_lanes(d, __ballot_sync(kFull, valid));
-            const uint32_t before = valid ? hist[w][d] : 0u;
+    // The digits are taken from the depth bits less the tile's smallest, r = d - dmin.
+    // First attempt: radix passes over the 16 highest bits of r's range [lo, hb) (two
+    // passes instead of up to four); keys equal in r >> lo are then ordered by the full key
+    // (depth, slot), run by run.  A tile with such a run longer than kTieRun is sorted again
+    // over every bit (lo = 0), which leaves only runs of equal depth.
+    const int hb = 32 - __clz(dmax - dmin);   // bit length of the range
+    int lo = max(0, hb - 16);
+    for (int attempt = 0; attempt < 2; attempt++) {
+        for (int shift = lo; shift < hb; shift += 8) {
+            for (int i = lane; i < 256; i += 32) hist[w][i] = 0u;
             __syncwarp();
-            if (valid) {
-                lrank[e] = (uint16_t)(before + __popc(peers & ((1u << lane) - 1u)));
-                if (lane == __ffs(peers) - 1) hist[w][d] = before + __popc(peers);
+            // count, and keep each key's rank among the equal digits of this warp's segment
+            // (earlier 32-key groups first, then lanes in order): the scatter below needs no
+            // ranking of its own
+            for (uint32_t c = seg0; c < seg1; c += 32) {
+                const uint32_t e = c + lane;
+                const bool valid = e < seg1;
+                const uint32_t d = valid ? ((((uint32_t)(src[e] >> 32) - dmin) >> shift) & 0xffu) : 0u;
+                const unsigned peers = same_digit_lanes(d, __ballot_sync(kFull, valid));
+                const uint32_t before = valid ? hist[w][d] : 0u;
+                __syncwarp();
+                if (valid) {
+                    lrank[e] = (uint16_t)(before + __popc(peers & ((1u << lane) - 1u)));
+                    if (lane == __ffs(peers) - 1) hist[w][d] = before + __popc(peers);
+                }
+                __syncwarp();
             }
-            __syncwarp();
-        }
-        __syncthreads();
-        {   // start of each (digit, warp) run: digit-major exclusive scan
-            const uint32_t dg = threadIdx.x;       // 256 threads = 256 digits
-            uint32_t cnts[kRsWarps], tot = 0u;
+            __syncthreads();
+            {   // start of each (digit, warp) run: digit-major exclusive scan
+                const uint32_t dg = threadIdx.x;       // 256 threads = 256 digits
+                uint32_t cnts[kRsWarps], tot = 0u;
 #pragma unroll
-            for (int i = 0; i < kRsWarps; i++) {
-                cnts[i] = hist[i][dg];
-                tot += cnts[i];
-            }
-            uint32_t off = block_excl_scan256(tot, wsum);
+                for (int i = 0; i < kRsWarps; i++) {
+                    cnts[i] = hist[i][dg];
+                    tot += cnts[i];
+                }
+                uint32_t off = block_excl_scan256(tot, wsum);
 #pragma unroll
-            for (int i = 0; i < kRsWarps; i++) {
-                hist[i][dg] = off;
-                off += cnts[i];
+                for (int i = 0; i < kRsWarps; i++) {
+                    hist[i][dg] = off;
+                    off += cnts[i];
+                }
+            }
+            __syncthreads();
+            for (uint32_t e = seg0 + lane; e < seg1; e += 32) {
+                const uint64_t k = src[e];
+                const uint32_t d = (((uint32_t)(k >> 32) - dmin) >> shift) & 0xffu;
+                dst[hist[w][d] + lrank[e]] = k;
+            }
+            __syncthreads();
+            uint64_t *tmp = src;
+            src = dst;
+            dst = tmp;
+        }
+        // runs of keys equal in depth bits lo..31: order by the full key (depth, slot);
+        // insertion sort by the run's first thread (runs are rare and short)
+        const bool check = lo > 0;
+        auto rkey = [&](uint32_t i) { return ((uint32_t)(src[i] >> 32) - dmin) >> lo; };
+        for (uint32_t i = threadIdx.x; i + 1 < len; i += kRsThreads) {
+            const uint32_t di = rkey(i);
+            const bool starts = (i == 0 || rkey(i - 1) != di) && rkey(i + 1) == di;
+            if (!starts) continue;
+            uint32_t e = i + 1;
+            while (e < len && rkey(e) == di) e++;
+            if (check && e - i > (uint32_t)kTieRun) {
+                s_long = 1;
+                continue;
+            }
+            for (uint32_t a = i + 1; a < e; a++) {
+                const uint64_t k = src[a];
+                uint32_t b = a;
+                while (b > i && src[b - 1] > k) {
+                    src[b] = src[b - 1];
+                    b--;
+                }
+                src[b] = k;
             }
         }
         __syncthreads();
-        for (uint32_t e = seg0 + lane; e < seg1; e += 32) {
-            const uint64_t k = src[e];
-            const uint32_t d = (uint32_t)(k >> (32 + shift)) & 0xffu;
-            dst[hist[w][d] + lrank[e]] = k;
-        }
+        if (!s_long) break;      // block-uniform
+        // a long run: sort the tile again over every bit of the range
+        for (uint32_t i = threadIdx.x; i < len; i += kRsThreads) bufA[i] = keys[st + i];
+        src = bufA;
+        dst = bufB;
+        lo = 0;
         __syncthreads();
-        uint64_t *tmp = src;
-        src = dst;
-        dst = tmp;
+        if (threadIdx.x == 0) s_long = 0;
     }
-    // runs of equal depth: order by slot (rare; insertion sort by the run's first thread)
-    for (uint32_t i = threadIdx.x; i + 1 < len; i += kRsThreads) {
-        const uint32_t di = (uint32_t)(src[i] >> 32);
-        const bool starts = (i == 0 || (uint32_t)(src[i - 1] >> 32) != di) && (uint32_t)(src[i + 1] >> 32) == di;
-        if (!starts) continue;
-        uint32_t e = i + 1;
-        while (e < len && (uint32_t)(src[e] >> 32) == di) e++;
-        for (uint32_t a = i + 1; a < e; a++) {
-            const uint64_t k = src[a];
-            uint32_t b = a;
-            while (b > i && src[b - 1] > k) {
-                src[b] = src[b - 1];
-                b--;
-            }
-            src[b] = k;
-        }
-    }
-    __syncthreads();
     for (uint32_t i = threadIdx.x; i < len; i += kRsThreads) vals[st + i] = (uint32_t)src[i];
 }
 

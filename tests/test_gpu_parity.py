@@ -141,6 +141,47 @@ def test_bin_sort_bit_exact(case):
     print(f"[bin {case}] instances {cnt} longest list {lens.max()}")
 
 
+def test_bin_sort_depth_ties_bit_exact():
+    """Depths the per-tile sort's first attempt cannot tell apart (it orders by the 16
+    highest bits of depth less the tile's smallest, over the tile's range): a run of 100
+    (the tile is sorted again over every bit), runs of two one ulp apart, exact duplicates
+    (slot order); a near and a far splat over every tile make the range wide."""
+    torch = torch_cuda()
+    N = native()
+    rng = np.random.default_rng(41)
+    W, H, B, n = 64, 48, 16, 1000
+    u = rng.uniform(0, W, n)
+    v = rng.uniform(0, H, n)
+    r = rng.integers(1, 9, n).astype(np.int32)
+    z = rng.uniform(0.5, 50.0, n).astype(np.float32)
+    u[:2], v[:2], r[:2], z[:2] = 32.0, 24.0, 100, (0.3, 60.0)
+    ulp4 = np.spacing(np.float32(4.0))
+    k = rng.permutation(100)
+    u[2:102], v[2:102], r[2:102] = rng.uniform(6, 10, 100), rng.uniform(6, 10, 100), 4
+    z[2:102] = np.float32(4.0) + k.astype(np.float32) * ulp4
+    d = rng.uniform(1.0, 50.0, 30).astype(np.float32)
+    pair = np.stack([d, np.nextafter(d, np.float32(np.inf))], 1).ravel()
+    u[102:162], v[102:162], r[102:162], z[102:162] = rng.uniform(36, 44, 60), rng.uniform(20, 28, 60), 4, pair
+    u[162:172], v[162:172], r[162:172] = rng.uniform(52, 60, 10), rng.uniform(36, 44, 10), 4
+    z[162:172] = np.repeat(rng.uniform(2.0, 30.0, 5).astype(np.float32), 2)
+    conic = np.zeros((n, 3), np.float32)
+    conic[:, 0] = conic[:, 2] = (3.0 / r.astype(np.float32)) ** 2
+    opac = np.full(n, 0.9)
+    rec10 = np.zeros((n, 10))
+    rec10[:, 0], rec10[:, 1], rec10[:, 9] = u, v, z
+    rec10[:, 2:5], rec10[:, 5] = conic, opac
+    g = rec_to_gpu(rec10, r)
+    cfg = N.make_config(W, H, B, 64, 0)
+    ranges_o, vals_o = O.bin_lists(u, v, z.astype(np.float64), r, 1, n, W, H, B, conic=conic, tau=O.tau32(opac))
+    cnt = len(vals_o)
+    lens = ranges_o[:, 1].astype(np.int64) - ranges_o[:, 0]
+    assert lens.max() < 2048 and lens[0] > 100     # the block-per-tile kernel; tile 0 holds the run of 100
+    vals, ranges, _, ninst, st = gpu_bin(N, g, n, 1, cfg, cnt + 3)
+    assert st == 0 and ninst == cnt
+    assert np.array_equal(ranges.cpu().numpy().view(np.uint32).reshape(-1, 2), ranges_o)
+    assert np.array_equal(vals.cpu().numpy().view(np.uint32)[:cnt], vals_o)
+
+
 def test_bin_sort_capacity_overflow_reports_and_truncates():
     torch = torch_cuda()
     N = native()
