@@ -73,6 +73,24 @@ __host__ __device__ constexpr int ppt_for()
     return (B * B / P >= 32) ? P : (B * B / 32);
 }
 
+// Tile row (0..B-1) of a thread's first pixel; its pixel p lies G p rows further down,
+// G = 32 / B the number of B-wide row groups a warp spans.  The warp's pixels with the
+// same p thus form a block of G adjacent rows (B = 16: rows 2p, 2p + 1 of the warp's
+// eight), so a splat that covers few rows leaves whole p-steps of the warp idle, where
+// rows p, p + 4 (consecutive rows per thread) would keep every p-step busy.
+template <int B, int P>
+__device__ __forceinline__ int thread_row0()
+{
+    constexpr int G = B >= 32 ? 1 : 32 / B;
+    const int grp = (int)threadIdx.x / B;
+    return (grp / G) * G * P + grp % G;
+}
+template <int B>
+__host__ __device__ constexpr int row_step()
+{
+    return B >= 32 ? 1 : 32 / B;
+}
+
 // Resident warps per SM each raster kernel is compiled for (__launch_bounds__ minimum
 // blocks): the register budget is 64K / (warps x 32), 64 registers at 32 warps.  Both
 // kernels are latency-bound and gain from more resident warps than their natural

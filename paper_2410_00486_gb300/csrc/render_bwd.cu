@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
     item_tile(a.order, a.g, tile, view, tx, ty);
     const int lane = threadIdx.x & 31;
     const int px = tx * B + (int)(threadIdx.x % B);
-    const int py0 = ty * B + (int)(threadIdx.x / B) * PPT;
+    constexpr int G = row_step<B>();
+    const int py0 = ty * B + thread_row0<B, PPT>();   // row of pixel p: py0 + G p
     const float fx = (float)px;
     const uint32_t start = a.ranges[2 * tile];
     const uint32_t len = a.ranges[2 * tile + 1] - start;
@@ -64,12 +65,12 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
     // (depth behind) gD, where "behind" starts as the background (no depth) and follows
     // R <- alpha c + (1 - alpha) R towards the front
     float T[PPT], gI0[PPT], gI1[PPT], gI2[PPT], gD[PPT], S[PPT];
-    const float fy0 = (float)py0;   // row of pixel p: fy0 + p (exact)
+    const float fy0 = (float)py0;   // row of pixel p: fy0 + G p (exact)
     uint32_t lst[PPT];
     uint32_t m = 0;
 #pragma unroll
     for (int p = 0; p < PPT; p++) {
-        const int py = py0 + p;
+        const int py = py0 + G * p;
         lst[p] = 0;
         T[p] = 1.f;
         gI0[p] = gI1[p] = gI2[p] = gD[p] = S[p] = 0.f;
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
             bool contrib = false;
 #pragma unroll
             for (int p = 0; p < PPT; p++) {
-                const float dy = __fsub_rn(q0.y, fy0 + (float)p);
+                const float dy = __fsub_rn(q0.y, fy0 + (float)(G * p));
                 const float power = power_at(pxs, q1.x, dy);
                 if (!(pos < lst[p]) || power > 0.f || power < q1.w) continue;
                 const float G = __expf(power);

@@ -26,7 +26,9 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
     int view, tx, ty;
     item_tile(a.order, a.g, tile, view, tx, ty);
     const int px = tx * B + (int)(threadIdx.x % B);
-    const int py0 = ty * B + (int)(threadIdx.x / B) * PPT;
+    constexpr int G = row_step<B>();
+    const int row0 = thread_row0<B, PPT>();
+    const int py0 = ty * B + row0;   // row of pixel p: py0 + G p
     const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
     const float fx = (float)px;
     // pixel-centre box of the tile (clipped to the image)
@@ -37,18 +39,18 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
     bool tdone = true;
 #pragma unroll
     for (int p = 0; p < PPT; p++) {
-        fy[p] = (float)(py0 + p);
+        fy[p] = (float)(py0 + G * p);
         T[p] = 1.f;
         C0[p] = C1[p] = C2[p] = D[p] = 0.f;
         lst[p] = 0;
-        done[p] = !(px < a.g.W && py0 + p < a.g.H);
+        done[p] = !(px < a.g.W && py0 + G * p < a.g.H);
         if (done[p]) fy[p] = kNoRow;
         tdone = tdone && done[p];
     }
     uint32_t n_eval = 0, n_blend = 0, active = 0;
     uint32_t next_ck = kBucket;   // next checkpoint boundary (list position)
     const int64_t ck_base = CKPT ? (int64_t)a.bucket_start[tile] : 0;
-    const int pix0 = (int)(threadIdx.x / B) * PPT * B + (int)(threadIdx.x % B);   // pixel index in the tile
+    const int pix0 = row0 * B + (int)(threadIdx.x % B);   // pixel index in the tile
 #pragma unroll
     for (int p = 0; p < PPT; p++) active += done[p] ? 0u : 1u;
     for (uint32_t base = start; base < end; base += BD) {
@@ -74,7 +76,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
                         if (bk < a.max_buckets) {
 #pragma unroll
                             for (int p = 0; p < PPT; p++) {
-                                const int64_t q = bk * (B * B) + pix0 + p * B;
+                                const int64_t q = bk * (B * B) + pix0 + G * p * B;
                                 a.ck4[q] = make_float4(T[p], C0[p], C1[p], C2[p]);
                                 a.ckD[q] = D[p];
                             }
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
     const size_t HW = (size_t)a.g.W * a.g.H;
 #pragma unroll
     for (int p = 0; p < PPT; p++) {
-        const int py = py0 + p;
+        const int py = py0 + G * p;
         if (!(px < a.g.W && py < a.g.H)) continue;
         const size_t q = (size_t)py * a.g.W + px;
         const size_t pix = (size_t)view * HW + q;
