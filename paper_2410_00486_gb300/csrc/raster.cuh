@@ -104,15 +104,27 @@ __host__ __device__ constexpr int min_blocks_for()
     return MinWarps / (B * B / ppt_for<B, P>() / 32) > 0 ? MinWarps / (B * B / ppt_for<B, P>() / 32) : 1;
 }
 
-// Staged splat, derived exactly from its record (negation and scaling by 1/2 are exact):
-//   s0 = (u, v, -A/2, -B), s1 = (-C/2, opacity, depth, tau), s2 = (r, g, b, -)
+// Staged splat, derived from its record with the exponent in base 2 (every term scaled
+// by log2 e, one rounding each), so alpha = opacity 2^power2 takes the hardware's base-2
+// exponential (PTX ex2.approx) and no multiply per pair:
+//   s0 = (u, v, -A/2 L, -B L), s1 = (-C/2 L, opacity, depth, tau L),  L = log2 e,
 // where tau = -ln(255 opacity): alpha = opacity exp(power) < 1/255 exactly when
-// power < tau, so both raster kernels test the exponent against tau and evaluate the
-// exponential only for pairs that can blend.
+// power < tau, so the raster kernels test the base-2 exponent against tau L and evaluate
+// the exponential only for pairs that can blend.
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
 __device__ __forceinline__ void stage_splat(const float4 &r0, const float4 &r1, float tau, float4 &t0, float4 &t1)
 {
-    t0 = make_float4(r0.x, r0.y, -0.5f * r0.z, -r0.w);
-    t1 = make_float4(-0.5f * r1.x, r1.y, r1.z, tau);
+    t0 = make_float4(r0.x, r0.y, __fmul_rn(r0.z, -0.5f * kLog2e), __fmul_rn(r0.w, -kLog2e));
+    t1 = make_float4(__fmul_rn(r1.x, -0.5f * kLog2e), r1.y, r1.z, __fmul_rn(tau, kLog2e));
+}
+
+// 2^x (PTX ex2.approx.ftz; x is at least tau L > -9 here, so nothing is flushed).
+__device__ __forceinline__ float exp2_fast(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // Exponent of the projected Gaussian at a pixel from a staged splat, with explicit

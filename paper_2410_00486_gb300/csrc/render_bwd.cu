@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
                 const float dy = __fsub_rn(q0.y, fy0 + (float)(G * p));
                 const float power = power_at(pxs, q1.x, dy);
                 if (!(pos < lst[p]) || power > 0.f || power < q1.w) continue;
-                const float G = __expf(power);
+                const float G = exp2_fast(power);
                 const float araw = __fmul_rn(q1.y, G);
                 const float alpha = fminf(kAlphaMax, araw);
                 contrib = true;
@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
                 if (contrib) {
                     float *g = a.sgrad + (size_t)sslot[j] * 12;
                     const float hA = q0.z, nB = q0.w, hC = q1.x;
-                    atomicAdd(g + 0, 2.f * hA * m0 + nB * sdpy);
-                    atomicAdd(g + 1, 2.f * hC * sdpy + nB * m0);
+                    atomicAdd(g + 0, kLn2 * (2.f * hA * m0 + nB * sdpy));   // staged terms carry log2 e
+                    atomicAdd(g + 1, kLn2 * (2.f * hC * sdpy + nB * m0));
                     atomicAdd(g + 2, -0.5f * (m0 * dx));
                     atomicAdd(g + 3, -m3);
                     atomicAdd(g + 4, -0.5f * sdpyy);
@@ -222,8 +222,8 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
                 //   dL/dA = -S_xx / 2, dL/dB = -S_xy, dL/dC = -S_yy / 2
                 // (staged q0.z = -A/2, q0.w = -B, q1.x = -C/2)
                 const float hC = q1.x;
-                if (f == 0) sum = 2.f * q0.z * sum + q0.w * other;
-                else if (f == 1) sum = 2.f * hC * sum + q0.w * other;
+                if (f == 0) sum = kLn2 * (2.f * q0.z * sum + q0.w * other);   // staged terms carry log2 e
+                else if (f == 1) sum = kLn2 * (2.f * hC * sum + q0.w * other);
                 else if (f == 2 || f == 4) sum = -0.5f * sum;
                 else if (f == 3) sum = -sum;
                 // record fields 0..6 (u, v, A, B, C, o, z), 8..10 (r, g, b)

@@ -187,7 +187,7 @@ k_render_bwd_splat(RasterBwdArgs a, const float4 *__restrict__ ck4, const float 
             const float dy = __fsub_rn(q0.y, (float)(ty * B + p / B));
             const float power = staged_power(q0, q1.x, dx, dy);
             if (power > 0.f || power < q1.w) continue;
-            const float G = __expf(power);
+            const float G = exp2_fast(power);
             const float araw = __fmul_rn(q1.y, G);
             const float alpha = fminf(kAlphaMax, araw);
             // the forward's blend step, bit for bit
@@ -223,8 +223,8 @@ k_render_bwd_splat(RasterBwdArgs a, const float4 *__restrict__ ck4, const float 
         if (keep) {
             float *gp = a.sgrad + (size_t)slot * 12;
             // staged q0.z = -A/2, q0.w = -B, q1.x = -C/2
-            atomicAdd(gp + 0, 2.f * q0.z * g0 + q0.w * g1);
-            atomicAdd(gp + 1, 2.f * q1.x * g1 + q0.w * g0);
+            atomicAdd(gp + 0, kLn2 * (2.f * q0.z * g0 + q0.w * g1));   // staged terms carry log2 e
+            atomicAdd(gp + 1, kLn2 * (2.f * q1.x * g1 + q0.w * g0));
             atomicAdd(gp + 2, -0.5f * g2);
             atomicAdd(gp + 3, -g3);
             atomicAdd(gp + 4, -0.5f * g4);

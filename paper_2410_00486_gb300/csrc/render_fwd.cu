@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
                     const float power = power_at(pxs, q1.x, __fsub_rn(q0.y, fy[p]));
                     // the alpha >= 1/255 test; a finished pixel (row NaN, so power NaN) fails it
                     if (!(power <= 0.f && power >= q1.w)) continue;
-                    const float alpha = fminf(kAlphaMax, __fmul_rn(q1.y, __expf(power)));
+                    const float alpha = fminf(kAlphaMax, __fmul_rn(q1.y, exp2_fast(power)));
                     const float wgt = __fmul_rn(alpha, T[p]);
                     const float testT = __fsub_rn(T[p], wgt);   // T (1 - alpha)
                     if (testT < kTMin) {
