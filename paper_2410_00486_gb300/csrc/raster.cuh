@@ -119,6 +119,14 @@ __device__ __forceinline__ void stage_splat(const float4 &r0, const float4 &r1, 
     t1 = make_float4(__fmul_rn(r1.x, -0.5f * kLog2e), r1.y, r1.z, __fmul_rn(tau, kLog2e));
 }
 
+// 1/x (PTX rcp.approx.ftz) for x = 1 - alpha in [0.01, 1].
+__device__ __forceinline__ float rcp_fast(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // 2^x (PTX ex2.approx.ftz; x is at least tau L > -9 here, so nothing is flushed).
 __device__ __forceinline__ float exp2_fast(float x)
 {

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
                 const float araw = __fmul_rn(q1.y, G);
                 const float alpha = fminf(kAlphaMax, araw);
                 contrib = true;
-                const float inv_om = __fdividef(1.f, __fsub_rn(1.f, alpha));
+                const float inv_om = rcp_fast(__fsub_rn(1.f, alpha));
                 T[p] = T[p] * inv_om;                             // transmittance before splat j
                 const float wT = alpha * T[p];
                 gr = fmaf(wT, gI0[p], gr);

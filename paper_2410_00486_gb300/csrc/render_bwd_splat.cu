@@ -195,7 +195,7 @@ k_render_bwd_splat(RasterBwdArgs a, const float4 *__restrict__ ck4, const float 
             const float n0 = fmaf(q2.x, wT, C0), n1 = fmaf(q2.y, wT, C1), n2 = fmaf(q2.z, wT, C2);
             const float nD = fmaf(q1.z, wT, D);
             const float4 ga = pA[p], fb = pB[p];
-            const float inv_om = __fdividef(1.f, __fsub_rn(1.f, alpha));
+            const float inv_om = rcp_fast(__fsub_rn(1.f, alpha));
             g8 += wT * ga.x;
             g9 += wT * ga.y;
             g10 += wT * ga.z;
