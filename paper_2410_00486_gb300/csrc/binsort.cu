@@ -126,17 +126,23 @@ constexpr int kAggThreads = 512;
 
 // Calls f(tile in view, key) for every tile of the rectangles of the visible slots [s0, s1)
 // of a view that the slot can reach (in_tile), row by row, load-balanced over the lanes of
-// each warp: a warp
-// takes 32 slots, forms the prefix sum of their row counts, and hands out rows
+// each warp: a warp takes the next group of 32 slots from the shared counter `next`
+// (groups differ widely in work), forms the prefix sum of their row counts, and hands out rows
 // round-robin; a lane finds the slot owning row j by a 5-step binary search over the
 // prefix (shuffles).  Slot order within a warp is kept, so a warp's calls for one tile
 // come in slot order within each round.
 template <class F>
 __device__ __forceinline__ void for_each_tile_row(const float4 *__restrict__ rec, int64_t n, int view, int64_t s0,
-                                                  int64_t s1, const Grid &g, F f)
+                                                  int64_t s1, const Grid &g, uint32_t *next, F f)
 {
     const int lane = threadIdx.x & 31;
-    for (int64_t wb = s0 + (int64_t)(threadIdx.x & ~31u); wb < s1; wb += blockDim.x) {   // warp-uniform
+    // warps take 32-slot groups from a shared counter (groups differ in work)
+    for (;;) {
+        uint32_t grp = 0;
+        if (lane == 0) grp = atomicAdd(next, 1u);
+        grp = __shfl_sync(kFull, grp, 0);
+        const int64_t wb = s0 + 32 * (int64_t)grp;
+        if (wb >= s1) break;
         const int64_t gi = wb + lane;
         int h = 0, x0 = 0, x1 = 0, y0 = 0;
         uint32_t zb = 0;
@@ -194,9 +200,11 @@ k_count_agg(const float4 *__restrict__ rec, int64_t n, Grid g, uint32_t *__restr
     const int view = blockIdx.y;
     const int64_t s0 = (int64_t)blockIdx.x * kChunk;
     const int64_t s1 = min(n, s0 + kChunk);
+    __shared__ uint32_t next;
     for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) hist[t] = 0;
+    if (threadIdx.x == 0) next = 0;
     __syncthreads();
-    for_each_tile_row(rec, n, view, s0, s1, g, [&](int t, uint64_t) { atomicAdd(&hist[t], 1u); });
+    for_each_tile_row(rec, n, view, s0, s1, g, &next, [&](int t, uint64_t) { atomicAdd(&hist[t], 1u); });
     __syncthreads();
     uint32_t *base = count + (int64_t)view * g.Tv;
     uint32_t *mine = bcount + ((int64_t)view * gridDim.x + blockIdx.x) * g.Tv;
@@ -298,12 +306,14 @@ k_scatter_agg(const float4 *__restrict__ rec, int64_t n, Grid g, const uint32_t 
     // this chunk's per-tile counts (from the count pass): reserve one run per tile
     const int64_t tbase = (int64_t)view * g.Tv;
     const uint32_t *mine = bcount + ((int64_t)view * gridDim.x + blockIdx.x) * g.Tv;
+    __shared__ uint32_t next;
+    if (threadIdx.x == 0) next = 0;
     for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) {
         const uint32_t c = mine[t];
         hist[t] = c ? start[tbase + t] + atomicAdd(cursor + tbase + t, c) : 0u;
     }
     __syncthreads();
-    for_each_tile_row(rec, n, view, s0, s1, g, [&](int t, uint64_t key) {
+    for_each_tile_row(rec, n, view, s0, s1, g, &next, [&](int t, uint64_t key) {
         const uint64_t pos = atomicAdd(&hist[t], 1u);
         if (pos < (uint64_t)capacity) keys[pos] = key;
     });
