@@ -41,13 +41,21 @@ __device__ __forceinline__ float lr_of(int64_t i, const AdamArgs &a)
     return lr;
 }
 
-// Bias corrections of the step held on the device, computed in double once per thread.
+// Bias corrections of the step held on the device, computed in double by one thread of
+// the block and shared (FP64 is slow on this part: a pow per thread cost more than the
+// whole element update).
 __device__ __forceinline__ void bias_corrections(AdamArgs &a)
 {
-    if (a.step_dev) {
-        const double t = (double)*a.step_dev;
-        a.rbc1 = (float)(1.0 / (1.0 - pow((double)a.b1, t)));
-        a.rbc2sqrt = (float)(1.0 / sqrt(1.0 - pow((double)a.b2, t)));
+    if (a.step_dev) {   // uniform over the grid
+        __shared__ float bc[2];
+        if (threadIdx.x == 0) {
+            const double t = (double)*a.step_dev;
+            bc[0] = (float)(1.0 / (1.0 - pow((double)a.b1, t)));
+            bc[1] = (float)(1.0 / sqrt(1.0 - pow((double)a.b2, t)));
+        }
+        __syncthreads();
+        a.rbc1 = bc[0];
+        a.rbc2sqrt = bc[1];
     }
 }
 
