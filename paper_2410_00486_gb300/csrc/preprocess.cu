@@ -16,6 +16,7 @@ constexpr int kGB = 128;         // Gaussians per block (64: backward 0.53 ms, 1
 constexpr int kPreThreads = 256;
 constexpr int kPreBwdMinBlocks = 2;   // resident blocks per SM the backward is compiled for
 constexpr int kViewChunk = 64;        // views per compaction round of the backward
+static_assert(kGB * kViewChunk / kPreThreads <= 32, "a thread's visibility bits of a view chunk fit one word");
 constexpr int kCamF = 23;        // staged camera: 20 ABI floats + camera centre
 
 // Real SH normalisation constants (closed forms: sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) x
@@ -460,14 +461,21 @@ k_preprocess_bwd(const float *__restrict__ P, int64_t n, const cgs_camera *__res
     for (int v0 = 0; v0 < V; v0 += kViewChunk) {
         const int nit = kGB * min(kViewChunk, V - v0);
         int nitems = 0;
-        for (int c0 = 0; c0 < nit; c0 += kPreThreads) {
+        // visibility of this thread's items of the chunk, all loads in flight together
+        // (one bit per round of kPreThreads items)
+        uint32_t vismask = 0;
+#pragma unroll 8
+        for (int c0 = 0, rb = 0; c0 < nit; c0 += kPreThreads, rb++) {
             const int it = c0 + (int)threadIdx.x;
             const int gl = it % kGB, v = v0 + it / kGB;
-            bool vis = false;
             if (it < nit && gl < cnt) {
                 const float *r = reinterpret_cast<const float *>(rec + kRec4 * ((int64_t)v * n + g0 + gl));
-                vis = __float_as_int(__ldg(r + 7)) > 0;
+                if (__float_as_int(__ldg(r + 7)) > 0) vismask |= 1u << rb;
             }
+        }
+        for (int c0 = 0, rb = 0; c0 < nit; c0 += kPreThreads, rb++) {
+            const int it = c0 + (int)threadIdx.x;
+            const bool vis = (vismask >> rb) & 1u;
             const unsigned b = __ballot_sync(kFull, vis);
             if (lane == 0) wcount[wp] = __popc(b);
             __syncthreads();
