@@ -90,8 +90,10 @@ __device__ __forceinline__ Rect tile_rect(float u, float v, int r, const Grid &g
 // ellipse's bounding box (half-extents sqrt(t2 C / det) + 0.01, sqrt(t2 A / det) + 0.01)
 // is tested first; then, with the centre outside the box, the minimum of q over the box,
 // which lies on an edge where q is a parabola minimised at its clamped vertex.  The
-// margins exceed the float32 error of the raster's per-pixel test (power < tau skips), so
-// a splat left out of a tile is one every pixel of the tile would skip.
+// margins exceed the float32 error of the raster's per-pixel test (power < tau skips)
+// unless the exponent's terms cancel by many orders of magnitude (a splat thousands of
+// pixels long and under a pixel wide), so a splat left out of a tile is one every pixel
+// of the tile would skip; the lists are defined by this test either way.
 __device__ __forceinline__ float edge_q(float A, float B2, float C, float ddx, float ddy)
 {
     return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, ddx), ddx), __fmul_rn(__fmul_rn(B2, ddx), ddy)),
@@ -145,20 +147,6 @@ __device__ __forceinline__ bool reach_box(const ReachPre &p, float u, float v, f
     return qmin <= p.t2;
 }
 
-// Exponent of the projected 2-D Gaussian at a pixel, written with explicit
-// roundings so the forward and backward kernels take bit-identical decisions:
-//   power = dx (-A/2 dx - B dy) + (-C/2 dy) dy,  (dx, dy) = (u - x, v - y).
-__device__ __forceinline__ float splat_power(float u, float v, float A, float B, float C,
-                                             float px, float py, float &dx, float &dy)
-{
-    dx = __fsub_rn(u, px);
-    dy = __fsub_rn(v, py);
-    float t = fmaf(-0.5f * A, dx, __fmul_rn(-B, dy));
-    float s = __fmul_rn(__fmul_rn(-0.5f * C, dy), dy);
-    return fmaf(dx, t, s);
-}
-
-constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 

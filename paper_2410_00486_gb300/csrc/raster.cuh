@@ -95,7 +95,7 @@ __host__ __device__ constexpr int row_step()
 // blocks): the register budget is 64K / (warps x 32), 64 registers at 32 warps.  Both
 // kernels are latency-bound and gain from more resident warps than their natural
 // register counts allow; the backward spills at 36 warps (56 registers) and measured
-// slower there (5.15 vs 4.88 ms on the 16-view window).
+// slower there, and the forward (56 registers) gains nothing from 36 or 40.
 constexpr int kFwdMinWarps = 32;
 constexpr int kBwdMinWarps = 32;
 template <int B, int P, int MinWarps>
