@@ -4,18 +4,23 @@
 // tile.  Instead of a global LSD radix sort over 64-bit (tile, depth) keys, which
 // reads and writes every instance once per digit pass, the sort here is
 // most-significant-digit first with the tile id as one full-width digit:
-//   1. k_count    : per-tile instance counts (atomic histogram over the rects)
-//   2. k_scan     : exclusive scan -> tile ranges (the digit's bucket offsets)
-//   3. k_scatter  : every instance is written once into its tile's bucket as the
-//                   64-bit key (depth bits << 32 | slot); the order inside a bucket
-//                   is arbitrary
-//   4. k_sort_*   : each bucket is sorted in shared memory.  The keys within a tile
-//                   are unique (a slot appears once per tile), so the result is one
-//                   well-defined order, (depth, slot) ascending, whatever order the
-//                   scatter produced.  Depth is positive, so its IEEE bits order
-//                   like its values.
+//   1. k_count_agg   : per (4096-slot chunk, tile) instance counts in shared memory; a
+//                      slot is counted in the tiles of its rect its alpha >= 1/255 ellipse
+//                      reaches (reach_box), and a slot with at most 64 rect tiles keeps
+//                      the decisions as a bit mask for step 3
+//   2. k_scan        : exclusive scan -> tile ranges (the digit's bucket offsets)
+//   3. k_scatter_agg : every instance is written once into its tile's bucket as the
+//                      64-bit key (depth bits << 32 | slot), in one reserved run per
+//                      (chunk, tile); the order inside a bucket is arbitrary
+//   4. k_sort_*      : each bucket is sorted in shared memory.  The keys within a tile
+//                      are unique (a slot appears once per tile), so the result is one
+//                      well-defined order, (depth, slot) ascending, whatever order the
+//                      scatter produced.  Depth is positive, so its IEEE bits order
+//                      like its values.
 // Buckets longer than kSmallCap go to a second kernel with a larger shared-memory
-// buffer; buckets beyond that are sorted in place in global memory by one block.
+// buffer; buckets beyond that are sorted in place in global memory by one block.  When a
+// view's tile histogram does not fit in shared memory, k_count / k_scatter do steps 1
+// and 3 with global atomics.
 #include <algorithm>
 
 #include "cgs_internal.cuh"
@@ -36,18 +41,20 @@ struct BinWs {
     uint32_t *nbig;      // [1]
     uint32_t *big;       // [Ttot]
     uint32_t *bcount;    // [chunks x Ttot]: per (slot chunk, tile) instance counts
+    uint64_t *masks;     // [V n]: per slot, the tiles of its rect that passed the reach test
     uint64_t *keys;      // [capacity]
 };
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Sections: counters (one memset), big-tile list, per-chunk counts (shared-memory path
-// only), keys.
-static size_t ws_layout(int64_t capacity, int64_t Ttot, int64_t chunk_counts, BinWs *w, void *base)
+// Sections: counters (one memset), big-tile list, per-chunk counts and per-slot tile
+// masks (shared-memory path only), keys.
+static size_t ws_layout(int64_t capacity, int64_t Ttot, int64_t chunk_counts, int64_t slots, BinWs *w, void *base)
 {
     size_t head = align256(sizeof(uint32_t) * (2 * (size_t)Ttot + 2));
     size_t bigb = align256(sizeof(uint32_t) * (size_t)Ttot);
     size_t chb = align256(sizeof(uint32_t) * (size_t)chunk_counts);
+    size_t mkb = chunk_counts > 0 ? align256(sizeof(uint64_t) * (size_t)slots) : 0;
     size_t keyb = align256(sizeof(uint64_t) * (size_t)(capacity > 0 ? capacity : 1));
     if (w && base) {
         char *b = static_cast<char *>(base);
@@ -56,9 +63,10 @@ static size_t ws_layout(int64_t capacity, int64_t Ttot, int64_t chunk_counts, Bi
         w->nbig = w->cursor + Ttot;
         w->big = reinterpret_cast<uint32_t *>(b + head);
         w->bcount = reinterpret_cast<uint32_t *>(b + head + bigb);
-        w->keys = reinterpret_cast<uint64_t *>(b + head + bigb + chb);
+        w->masks = reinterpret_cast<uint64_t *>(b + head + bigb + chb);
+        w->keys = reinterpret_cast<uint64_t *>(b + head + bigb + chb + mkb);
     }
-    return head + bigb + chb + keyb;
+    return head + bigb + chb + mkb + keyb;
 }
 
 // Per-(chunk, tile) counts kept between the count and scatter passes when a view's tile
@@ -71,7 +79,7 @@ static int64_t chunk_count_entries(int64_t n, int64_t V, int64_t Tv)
 
 size_t bin_ws_bytes(int64_t capacity, int64_t n, int64_t V, int64_t Tv)
 {
-    return ws_layout(capacity, Tv * V, chunk_count_entries(n, V, Tv), nullptr, nullptr);
+    return ws_layout(capacity, Tv * V, chunk_count_entries(n, V, Tv), V * n, nullptr, nullptr);
 }
 
 __device__ __forceinline__ bool load_slot(const float4 *__restrict__ rec, int64_t slot, float &u, float &v,
@@ -127,13 +135,19 @@ constexpr int kAggThreads = 512;
 // Calls f(tile in view, key) for every tile of the rectangles of the visible slots [s0, s1)
 // of a view that the slot can reach (in_tile), row by row, load-balanced over the lanes of
 // each warp: a warp takes the next group of 32 slots from the shared counter `next`
-// (groups differ widely in work), forms the prefix sum of their row counts, and hands out rows
-// round-robin; a lane finds the slot owning row j by a 5-step binary search over the
-// prefix (shuffles).  Slot order within a warp is kept, so a warp's calls for one tile
-// come in slot order within each round.
-template <class F>
+// (groups differ widely in work), forms the prefix sum of their row counts, and hands out
+// rows round-robin; a lane finds the slot owning row j by a 5-step binary search over the
+// prefix (shuffles).
+// Tile masks: a slot whose rect has at most 64 tiles keeps one bit per tile (row-major over
+// the rect) saying whether it passed the reach test.  The count pass (RECORD) sets them
+// (wm: this warp's 32 shared words) and stores them per slot; the scatter pass (!RECORD)
+// reads them back instead of testing again, and tests only the slots with larger rects.
+constexpr int kMaskTiles = 64;
+
+template <bool RECORD, class F>
 __device__ __forceinline__ void for_each_tile_row(const float4 *__restrict__ rec, int64_t n, int view, int64_t s0,
-                                                  int64_t s1, const Grid &g, uint32_t *next, F f)
+                                                  int64_t s1, const Grid &g, uint32_t *next,
+                                                  unsigned long long *wm, uint64_t *__restrict__ masks, F f)
 {
     const int lane = threadIdx.x & 31;
     // warps take 32-slot groups from a shared counter (groups differ in work)
@@ -160,6 +174,14 @@ __device__ __forceinline__ void for_each_tile_row(const float4 *__restrict__ rec
                 e = load_reach(rec, (int64_t)view * n + gi);
             }
         }
+        const bool small = h * (x1 - x0) <= kMaskTiles;
+        unsigned long long mk = 0ull;
+        if (RECORD) {
+            wm[lane] = 0ull;
+            __syncwarp();
+        } else if (gi < s1 && h > 0 && small) {
+            mk = masks[(int64_t)view * n + gi];
+        }
         int incl = h;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -178,24 +200,50 @@ __device__ __forceinline__ void for_each_tile_row(const float4 *__restrict__ rec
             const int oy0 = __shfl_sync(kFull, y0, L);
             const uint32_t ozb = __shfl_sync(kFull, zb, L);
             const float ou = __shfl_sync(kFull, u, L), ov = __shfl_sync(kFull, v, L);
-            const ReachPre oe{__shfl_sync(kFull, e.A, L),  __shfl_sync(kFull, e.B2, L), __shfl_sync(kFull, e.C, L),
+            const bool osmall = __shfl_sync(kFull, small, L);
+            const unsigned long long omk = RECORD ? 0ull : __shfl_sync(kFull, mk, L);
+            const bool test = j < total && (RECORD || !osmall);
+            ReachPre oe{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+            if (__any_sync(kFull, test))
+                oe = ReachPre{__shfl_sync(kFull, e.A, L),  __shfl_sync(kFull, e.B2, L), __shfl_sync(kFull, e.C, L),
                               __shfl_sync(kFull, e.t2, L), __shfl_sync(kFull, e.ex, L), __shfl_sync(kFull, e.ey, L),
                               __shfl_sync(kFull, e.bc, L), __shfl_sync(kFull, e.ba, L), __shfl_sync(kFull, e.mode, L)};
             if (j < total) {
                 const uint32_t slot = (uint32_t)((int64_t)view * n + wb + L);
                 const uint64_t key = ((uint64_t)ozb << 32) | (uint64_t)slot;
-                const int ty = oy0 + (j - (oend - oh));
-                for (int tx = ox0; tx < ox1; tx++)
-                    if (in_tile(oe, ou, ov, tx, ty, g)) f(ty * g.Tx + tx, key);
+                const int row = j - (oend - oh), ty = oy0 + row, ow = ox1 - ox0;
+                if (!RECORD && osmall) {
+                    // the count pass's decisions for this row
+                    unsigned long long bits = (omk >> (row * ow)) & (ow >= 64 ? ~0ull : ((1ull << ow) - 1ull));
+                    while (bits) {
+                        const int b = __ffsll((long long)bits) - 1;
+                        bits &= bits - 1ull;
+                        f(ty * g.Tx + ox0 + b, key);
+                    }
+                } else {
+                    unsigned long long rowbits = 0ull;
+                    for (int tx = ox0; tx < ox1; tx++)
+                        if (in_tile(oe, ou, ov, tx, ty, g)) {
+                            f(ty * g.Tx + tx, key);
+                            if (RECORD && osmall) rowbits |= 1ull << (tx - ox0);   // tx - ox0 < 64
+                        }
+                    if (RECORD && osmall && rowbits) atomicOr(&wm[L], rowbits << (row * ow));
+                }
             }
+        }
+        if (RECORD) {
+            __syncwarp();
+            if (gi < s1 && h > 0 && small) masks[(int64_t)view * n + gi] = wm[lane];
+            __syncwarp();
         }
     }
 }
 
 __global__ void __launch_bounds__(kAggThreads)
 k_count_agg(const float4 *__restrict__ rec, int64_t n, Grid g, uint32_t *__restrict__ count,
-            uint32_t *__restrict__ bcount)
+            uint32_t *__restrict__ bcount, uint64_t *__restrict__ masks)
 {
+    __shared__ unsigned long long wmask[kAggThreads / 32][32];
     extern __shared__ uint32_t hist[];
     const int view = blockIdx.y;
     const int64_t s0 = (int64_t)blockIdx.x * kChunk;
@@ -204,7 +252,8 @@ k_count_agg(const float4 *__restrict__ rec, int64_t n, Grid g, uint32_t *__restr
     for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) hist[t] = 0;
     if (threadIdx.x == 0) next = 0;
     __syncthreads();
-    for_each_tile_row(rec, n, view, s0, s1, g, &next, [&](int t, uint64_t) { atomicAdd(&hist[t], 1u); });
+    for_each_tile_row<true>(rec, n, view, s0, s1, g, &next, wmask[threadIdx.x >> 5], masks,
+                            [&](int t, uint64_t) { atomicAdd(&hist[t], 1u); });
     __syncthreads();
     uint32_t *base = count + (int64_t)view * g.Tv;
     uint32_t *mine = bcount + ((int64_t)view * gridDim.x + blockIdx.x) * g.Tv;
@@ -296,8 +345,8 @@ __global__ void k_scatter(const float4 *__restrict__ rec, int64_t n, int V, Grid
 // single global atomic, then places its instances with shared-memory atomics.
 __global__ void __launch_bounds__(kAggThreads)
 k_scatter_agg(const float4 *__restrict__ rec, int64_t n, Grid g, const uint32_t *__restrict__ start,
-              uint32_t *__restrict__ cursor, const uint32_t *__restrict__ bcount, uint64_t *__restrict__ keys,
-              int64_t capacity)
+              uint32_t *__restrict__ cursor, const uint32_t *__restrict__ bcount, uint64_t *__restrict__ masks,
+              uint64_t *__restrict__ keys, int64_t capacity)
 {
     extern __shared__ uint32_t hist[];     // [Tv] counts, then run positions
     const int view = blockIdx.y;
@@ -313,7 +362,7 @@ k_scatter_agg(const float4 *__restrict__ rec, int64_t n, Grid g, const uint32_t 
         hist[t] = c ? start[tbase + t] + atomicAdd(cursor + tbase + t, c) : 0u;
     }
     __syncthreads();
-    for_each_tile_row(rec, n, view, s0, s1, g, &next, [&](int t, uint64_t key) {
+    for_each_tile_row<false>(rec, n, view, s0, s1, g, &next, nullptr, masks, [&](int t, uint64_t key) {
         const uint64_t pos = atomicAdd(&hist[t], 1u);
         if (pos < (uint64_t)capacity) keys[pos] = key;
     });
@@ -650,7 +699,7 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
 {
     const int64_t Ttot = g.Tv * V;
     BinWs w;
-    ws_layout(capacity, Ttot, chunk_count_entries(n, V, g.Tv), &w, ws);
+    ws_layout(capacity, Ttot, chunk_count_entries(n, V, g.Tv), (int64_t)V * n, &w, ws);
     const float4 *r4 = reinterpret_cast<const float4 *>(rec);
     cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (2 * (size_t)Ttot + 2), s);
     if (e != cudaSuccess) return e;
@@ -667,13 +716,13 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((slots + threads - 1) / threads, (int64_t)num_sms * 16);
     if (agg)
-        k_count_agg<<<agrid, kAggThreads, hist_bytes, s>>>(r4, n, g, w.count, w.bcount);
+        k_count_agg<<<agrid, kAggThreads, hist_bytes, s>>>(r4, n, g, w.count, w.bcount, w.masks);
     else
         k_count<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count);
     k_scan<<<1, 1024, 0, s>>>(w.count, Ttot, capacity, ranges, n_inst, status);
     if (agg)
-        k_scatter_agg<<<agrid, kAggThreads, hist_bytes, s>>>(r4, n, g, w.count, w.cursor, w.bcount, w.keys,
-                                                             capacity);
+        k_scatter_agg<<<agrid, kAggThreads, hist_bytes, s>>>(r4, n, g, w.count, w.cursor, w.bcount, w.masks,
+                                                             w.keys, capacity);
     else
         k_scatter<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count, w.cursor, w.keys, capacity);
     k_sort_tiles<<<(unsigned)Ttot, kRsThreads, 0, s>>>(ranges, w.keys, vals, w.big, w.nbig);

@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
         }
         __syncthreads();
         if (!tdone) {
+#pragma unroll 4
             for (int j = 0; j < cnt; j++) {
                 const uint32_t pos = base - start + (uint32_t)j;   // list position of splat j
                 if (CKPT) {
