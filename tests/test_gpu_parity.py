@@ -282,6 +282,36 @@ def test_render_fwd_matches_oracle(name, bd):
     print(f"[fwd {name}] excluded {frac:.2e} max|dimg| {e_img:.2e} |dT| {e_T:.2e} |ddepth|/scale {e_d:.2e}")
 
 
+def test_render_fwd_work_counts_on_request():
+    """cgs_config.count_work compiles the blended-pair counter in: the images are bit-identical
+    with and without it, the per-tile evaluated counts agree, and the blended count (partial
+    4) is zero without it and at most the evaluated count with it."""
+    torch = torch_cuda()
+    N = native()
+    sc, tgt_rgb, tgt_d, pre, rec, ranges, vals, fw = stage_inputs("room_sh3_20k")
+    out = gpu_forward_from_rec(N, sc, rec, pre, tgt_rgb, tgt_d, 128, cap=len(vals) + 16)
+    V = sc.views
+    Ttot = N.cgs_tiles_per_view(out["cfg"]) * V
+    res = {}
+    for cw in (False, True):
+        cfg = N.make_config(sc.width, sc.height, sc.tile, 128, sc.sh_degree, 0.2, (0.0, 0.0, 0.0), 0.1,
+                            count_work=cw)
+        ws = torch.empty(N.cgs_render_fwd_workspace(V, cfg), dtype=torch.uint8, device="cuda")
+        img, depth, T = torch.zeros_like(out["img"]), torch.zeros_like(out["depth"]), torch.zeros_like(out["T"])
+        last, loss, dc = torch.zeros_like(out["last"]), torch.zeros_like(out["loss"]), torch.zeros_like(out["dcount"])
+        N.cgs_render_fwd(out["rec"], out["vals"], out["ranges"], out["order"], V, cfg, out["w"], out["tr"],
+                         out["td"], img, depth, T, last, loss, dc, ws)
+        torch.cuda.synchronize()
+        part = ws[: 4 * 5 * Ttot].view(torch.float32).view(Ttot, 5).cpu().numpy()
+        res[cw] = (img.cpu().numpy(), depth.cpu().numpy(), T.cpu().numpy(), last.cpu().numpy(), part)
+    for a, b in zip(res[False][:4], res[True][:4]):
+        assert np.array_equal(a, b)
+    p0, p1 = res[False][4], res[True][4]
+    assert np.array_equal(p0[:, 3], p1[:, 3]) and p1[:, 3].sum() > 0
+    assert np.all(p0[:, 4] == 0)
+    assert np.all(p1[:, 4] <= p1[:, 3]) and p1[:, 4].sum() > 0
+
+
 def test_render_fwd_background_and_ragged_tiles():
     N = native()
     bg = (0.2, 0.5, 0.9)
