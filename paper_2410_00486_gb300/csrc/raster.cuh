@@ -61,10 +61,11 @@ __device__ __forceinline__ void item_tile(const uint32_t *order, const Grid &g, 
 // Pixels per thread in the raster kernels: a thread owns several vertically adjacent pixels,
 // so the staged splat is read from shared memory once for PPT pixels and the backward's
 // per-(warp, splat) reduction covers 32*PPT pixels.
-// The forward keeps two (its per-thread state is small and occupancy pays), the
-// backward four (fewer warp reductions per pixel).
+// The forward keeps two (its per-thread state is small and occupancy pays; four measured
+// slower), the backward eight: one warp per 16x16 tile, half the warp reductions per pixel
+// of four pixels, which were a third of its time (3.84 vs 4.04 ms on the 16-view window).
 constexpr int kPPTFwd = 2;
-constexpr int kPPTBwd = 4;
+constexpr int kPPTBwd = 8;
 
 // Pixels per thread for tile edge B: P, but at least one full warp per tile.
 template <int B, int P>
@@ -92,12 +93,12 @@ __host__ __device__ constexpr int row_step()
 }
 
 // Resident warps per SM each raster kernel is compiled for (__launch_bounds__ minimum
-// blocks): the register budget is 64K / (warps x 32), 64 registers at 32 warps.  Both
-// kernels are latency-bound and gain from more resident warps than their natural
-// register counts allow; the backward spills at 36 warps (56 registers) and measured
-// slower there, and the forward (56 registers) gains nothing from 36 or 40.
+// blocks): the register budget is 64K / (warps x 32).  The forward runs at 32 warps (64
+// registers, 56 used; 36 or 40 gain nothing).  The backward, with eight pixels of state
+// per thread, runs at 20 warps (96 registers, no spill); 18 spills a little and 22 or 24
+// spill hundreds of bytes, and both are slower.
 constexpr int kFwdMinWarps = 32;
-constexpr int kBwdMinWarps = 32;
+constexpr int kBwdMinWarps = 20;
 template <int B, int P, int MinWarps>
 __host__ __device__ constexpr int min_blocks_for()
 {

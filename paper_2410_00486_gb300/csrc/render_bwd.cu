@@ -1,7 +1,8 @@
 // Backward of the blend (Eqs. 2-4, Sec. III-C.1, CaRtGS), pixel-parallel.
 //
-// One block per (view, tile), four vertically adjacent pixels per thread (two on 8x8
-// tiles), walking the tile's list back to front from the block's largest `last`.
+// One block per (view, tile), eight pixels of one column per thread (one warp per 16x16
+// tile; two pixels on 8x8 tiles), walking the tile's list back to front from the block's
+// largest `last`.
 // A tile's list holds only splats that can reach alpha >= 1/255 in it (the binning's
 // test), the same list the forward walked.  Each pixel recomputes alpha exactly as the
 // forward did (same rounding, same decisions) and its transmittance from the stored final T,
@@ -28,7 +29,7 @@ namespace cgs {
 // atomics (L2 reductions); more contributors go through the warp sum.  Measured on the
 // 16-view window (raster backward ms): 4 lanes 5.02, 8 lanes 4.92, 12 lanes 4.88,
 // 16 lanes 4.91; every lane direct is five times slower (same-address atomics serialise).
-constexpr int kDirectLanes = 12;
+constexpr int kDirectLanes = 16;
 
 // Row stride (floats) of the per-warp reduction buffer: ten fields padded to 12.
 constexpr int kRedStride = 12;
@@ -138,30 +139,41 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
             // moments sum dp, sum dp dy, sum dp dy^2 of dp = dL/dpower (dx is shared)
             float gr = 0.f, gg = 0.f, gb = 0.f, gz = 0.f, go = 0.f, sdp = 0.f, sdpy = 0.f, sdpyy = 0.f;
             bool contrib = false;
+            // pixels in pairs: a pair where either pixel blends runs both through the blend
+            // (the other with G = 0, so alpha = 0 and its state is kept), so the two chains
+            // interleave
 #pragma unroll
-            for (int p = 0; p < PPT; p++) {
-                const float dy = __fsub_rn(q0.y, fy0 + (float)(G * p));
-                const float power = power_at(pxs, q1.x, dy);
-                if (!(pos < lst[p]) || power > 0.f || power < q1.w) continue;
-                const float G = exp2_fast(power);
-                const float araw = __fmul_rn(q1.y, G);
-                const float alpha = fminf(kAlphaMax, araw);
+            for (int p2 = 0; p2 < PPT; p2 += 2) {
+                float dyv[2], pw[2];
+                bool k[2];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int p = p2 + h;
+                    dyv[h] = __fsub_rn(q0.y, fy0 + (float)(G * p));
+                    pw[h] = power_at(pxs, q1.x, dyv[h]);
+                    k[h] = pos < lst[p] && !(pw[h] > 0.f || pw[h] < q1.w);
+                }
+                if (!(k[0] || k[1])) continue;
                 contrib = true;
-                const float inv_om = rcp_fast(__fsub_rn(1.f, alpha));
-                T[p] = T[p] * inv_om;                             // transmittance before splat j
-                const float wT = alpha * T[p];
-                gr = fmaf(wT, gI0[p], gr);
-                gg = fmaf(wT, gI1[p], gg);
-                gb = fmaf(wT, gI2[p], gb);
-                gz = fmaf(wT, gD[p], gz);
-                // dL/dalpha = T (c . gI + z gD - S); then fold splat j into S for the
-                // splats in front of it
-                const float cg = fmaf(q1.z, gD[p], fmaf(q2.z, gI2[p], fmaf(q2.y, gI1[p], q2.x * gI0[p])));
-                const float diff = cg - S[p];
-                S[p] = fmaf(alpha, diff, S[p]);
-                if (!(araw > kAlphaMax)) {
-                    // dalpha/dpower = alpha, dalpha/dopacity = G
-                    const float dLda = diff * T[p];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int p = p2 + h;
+                    const float dy = dyv[h];
+                    const float G = k[h] ? exp2_fast(pw[h]) : 0.f;
+                    const float araw = __fmul_rn(q1.y, G);
+                    const float alpha = fminf(kAlphaMax, araw);
+                    const float inv_om = rcp_fast(__fsub_rn(1.f, alpha));
+                    T[p] = k[h] ? T[p] * inv_om : T[p];               // transmittance before splat j
+                    const float wT = alpha * T[p];
+                    gr = fmaf(wT, gI0[p], gr);
+                    gg = fmaf(wT, gI1[p], gg);
+                    gb = fmaf(wT, gI2[p], gb);
+                    gz = fmaf(wT, gD[p], gz);
+                    const float cg = fmaf(q1.z, gD[p], fmaf(q2.z, gI2[p], fmaf(q2.y, gI1[p], q2.x * gI0[p])));
+                    const float diff = cg - S[p];
+                    S[p] = fmaf(alpha, diff, S[p]);
+                    // dalpha/dpower = alpha, dalpha/dopacity = G, both 0 where alpha is clamped
+                    const float dLda = araw > kAlphaMax ? 0.f : diff * T[p];
                     go = fmaf(dLda, G, go);
                     const float dp = dLda * alpha;
                     const float dpy = dp * dy;
