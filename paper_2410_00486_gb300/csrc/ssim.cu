@@ -52,23 +52,28 @@ k_ssim_fwd(const float *__restrict__ img, const float *__restrict__ tgt, int W, 
     // horizontal pass, kRB adjacent outputs per thread from kRB + 10 staged values
     for (int i = threadIdx.x; i < kSsimIn * (kSsimT / kRB); i += blockDim.x) {
         const int r = i / (kSsimT / kRB), c0 = (i % (kSsimT / kRB)) * kRB;
-        float xs[kRB + 2 * kSsimR], ys[kRB + 2 * kSsimR];
+        // the staged values and their products, formed once for the kRB outputs
+        float xs[kRB + 2 * kSsimR], ys[kRB + 2 * kSsimR], xx[kRB + 2 * kSsimR], yy[kRB + 2 * kSsimR],
+            xy[kRB + 2 * kSsimR];
 #pragma unroll
         for (int k = 0; k < kRB + 2 * kSsimR; k++) {
             xs[k] = sx[r][c0 + k];
             ys[k] = sy[r][c0 + k];
+            xx[k] = xs[k] * xs[k];
+            yy[k] = ys[k] * ys[k];
+            xy[k] = xs[k] * ys[k];
         }
 #pragma unroll
         for (int o = 0; o < kRB; o++) {
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
 #pragma unroll
             for (int k = 0; k < 2 * kSsimR + 1; k++) {
-                const float xv = xs[o + k], yv = ys[o + k], w = t.g[k];
-                a0 = fmaf(w, xv, a0);
-                a1 = fmaf(w, yv, a1);
-                a2 = fmaf(w, xv * xv, a2);
-                a3 = fmaf(w, yv * yv, a3);
-                a4 = fmaf(w, xv * yv, a4);
+                const float w = t.g[k];
+                a0 = fmaf(w, xs[o + k], a0);
+                a1 = fmaf(w, ys[o + k], a1);
+                a2 = fmaf(w, xx[o + k], a2);
+                a3 = fmaf(w, yy[o + k], a3);
+                a4 = fmaf(w, xy[o + k], a4);
             }
             hm[0][r][c0 + o] = a0;
             hm[1][r][c0 + o] = a1;
@@ -105,9 +110,9 @@ k_ssim_fwd(const float *__restrict__ img, const float *__restrict__ tgt, int W, 
             const float sxx = mom[2][o] - mx * mx, syy = mom[3][o] - my * my, sxy = mom[4][o] - mx * my;
             const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
             const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
-            const float inv = 1.f / (B1 * B2);
+            const float inv = __fdividef(1.f, B1 * B2);
             const float S = A1 * A2 * inv;
-            const float dA1 = A2 * inv, dA2 = A1 * inv, dB1 = -S / B1, dB2 = -S / B2;
+            const float dA1 = A2 * inv, dA2 = A1 * inv, dB1 = -S * (B2 * inv), dB2 = -S * (B1 * inv);
             const size_t q = plane + (size_t)gy * W + gx;
             amap[q] = 2.f * my * (dA1 - dA2) + 2.f * mx * (dB1 - dB2);
             bmap[q] = dB2;
