@@ -27,8 +27,7 @@
 
 namespace cgs {
 
-constexpr int kSmallCap = 2048;      // keys per tile sorted by the 256-thread kernel
-constexpr int kSmallThreads = 256;
+constexpr int kSmallCap = 2048;      // keys per tile sorted in shared memory by k_sort_tiles
 constexpr int kBigThreads = 1024;
 constexpr int kBigCap = 16384;       // keys held in shared memory by the big-tile kernel
 constexpr uint64_t kPadKey = ~0ull;  // larger than any real key
@@ -595,30 +594,6 @@ k_sort_tiles(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ k
         if (threadIdx.x == 0) s_long = 0;
     }
     for (uint32_t i = threadIdx.x; i < len; i += kRsThreads) vals[st + i] = (uint32_t)src[i];
-}
-
-__global__ void __launch_bounds__(kSmallThreads)
-k_sort_small(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-             uint32_t *__restrict__ big, uint32_t *__restrict__ nbig)
-{
-    __shared__ uint64_t s[kSmallCap];
-    const int64_t t = blockIdx.x;
-    const uint32_t st = ranges[2 * t], en = ranges[2 * t + 1];
-    const uint32_t len = en - st;
-    if (len == 0) return;
-    if (len > kSmallCap) {
-        if (threadIdx.x == 0) big[atomicAdd(nbig, 1u)] = (uint32_t)t;
-        return;
-    }
-    if (len == 1) {
-        if (threadIdx.x == 0) vals[st] = (uint32_t)keys[st];
-        return;
-    }
-    const uint32_t P = next_pow2(len);
-    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < len ? keys[st + i] : kPadKey;
-    __syncthreads();
-    smem_bitonic(s, P);
-    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) vals[st + i] = (uint32_t)s[i];
 }
 
 __global__ void __launch_bounds__(kBigThreads)
