@@ -27,8 +27,9 @@ namespace cgs {
 
 // Splats to which at most this many lanes of a warp contribute are added with per-lane
 // atomics (L2 reductions); more contributors go through the warp sum.  Measured on the
-// 16-view window (raster backward ms): 4 lanes 5.02, 8 lanes 4.92, 12 lanes 4.88,
-// 16 lanes 4.91; every lane direct is five times slower (same-address atomics serialise).
+// 16-view window with eight pixels per thread (raster backward ms): 4 lanes 3.94, 8 lanes
+// 3.87, 16 lanes 3.81, 20 lanes 3.93, 24 lanes 4.04; folding a half-warp onto the other
+// and adding from 16 lanes is twice as slow (same-address atomics serialise).
 constexpr int kDirectLanes = 16;
 
 // Row stride (floats) of the per-warp reduction buffer: ten fields padded to 12.
