@@ -657,9 +657,8 @@ def end_to_end(win, sc, cams, tgt_rgb, tgt_d, args, torch, N):
     def one_step():
         # the draws need the previous window's losses (reported below); the next window's
         # cameras and targets do not, so their copy is staged while this iteration runs
-        counts = np.zeros(V, np.float32)
-        for _ in range(V):
-            counts[sched.draw(int(rng.integers(0, 2 ** 32)))] += 1.0
+        counts = np.bincount(sched.draw_n(rng.integers(0, 2 ** 32, V, dtype=np.uint64).astype(np.uint32)),
+                             minlength=V).astype(np.float32)
         h_w.copy_(torch.from_numpy(counts))
         win.set_view_weight(h_w)
         win.commit_window()
@@ -668,9 +667,8 @@ def end_to_end(win, sc, cams, tgt_rgb, tgt_d, args, torch, N):
         done.record()
         win.stage_window(h_cams, h_rgb, h_d)
         done.synchronize()
-        for v in range(V):
-            if counts[v] > 0:
-                sched.report(v, float(h_loss[v]) / counts[v])
+        drawn = np.nonzero(counts)[0]
+        sched.report_n(drawn, h_loss.numpy()[drawn].astype(np.float64) / counts[drawn])
 
     win.stage_window(h_cams, h_rgb, h_d)
     for _ in range(args.warmup):

@@ -403,6 +403,13 @@ void cgs_sched_destroy(cgs_scheduler *s);
 int cgs_sched_add(cgs_scheduler *s, int32_t keyframe_id, int32_t r0);  /* returns pool index */
 int cgs_sched_draw(cgs_scheduler *s, uint32_t rand_u32);             /* returns pool index */
 int cgs_sched_report(cgs_scheduler *s, int32_t index, double loss);
+/* n draws in a row, exactly as n calls of cgs_sched_draw with rand_u32[0..n-1]: out[i]
+ * receives the i-th pool index.  Returns CGS_OK, or the first error (out is then filled
+ * up to that draw).  One call per window instead of one per view keeps the host's share of
+ * a training step small. */
+int cgs_sched_draw_n(cgs_scheduler *s, const uint32_t *rand_u32, int32_t n, int32_t *out);
+/* n reports, exactly as n calls of cgs_sched_report(s, index[i], loss[i]). */
+int cgs_sched_report_n(cgs_scheduler *s, const int32_t *index, const double *loss, int32_t n);
 /* copies keyframe ids, r and l of the first `cap` pool entries; returns the pool size */
 int cgs_sched_state(const cgs_scheduler *s, int32_t *ids, int32_t *r, double *l, int32_t cap);
 

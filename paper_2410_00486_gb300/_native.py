@@ -11,6 +11,7 @@ import ctypes
 from ctypes import POINTER, byref, c_double, c_float, c_int32, c_int64, c_size_t, c_uint32, c_void_p
 from pathlib import Path
 
+import numpy as np
 import torch
 
 LIB_PATH = Path(__file__).resolve().parent / "_build" / "libcgs.so"
@@ -91,6 +92,8 @@ _SIGS = {
     "cgs_sched_add": (c_int32, [_P, c_int32, c_int32]),
     "cgs_sched_draw": (c_int32, [_P, c_uint32]),
     "cgs_sched_report": (c_int32, [_P, c_int32, c_double]),
+    "cgs_sched_draw_n": (c_int32, [_P, _P, c_int32, _P]),
+    "cgs_sched_report_n": (c_int32, [_P, _P, _P, c_int32]),
     "cgs_sched_state": (c_int32, [_P, POINTER(c_int32), POINTER(c_int32), POINTER(c_double), c_int32]),
     "cgs_status_string": (ctypes.c_char_p, [c_int32]),
 }
@@ -336,6 +339,21 @@ class Scheduler:
 
     def report(self, index: int, loss: float):
         _check("cgs_sched_report", lib().cgs_sched_report(self._h, index, float(loss)))
+
+    def draw_n(self, rand_u32) -> np.ndarray:
+        """len(rand_u32) draws in one call; returns the pool indices (int32)."""
+        r = np.ascontiguousarray(rand_u32, dtype=np.uint32)
+        out = np.empty(r.size, dtype=np.int32)
+        _check("cgs_sched_draw_n", lib().cgs_sched_draw_n(self._h, r.ctypes.data, r.size, out.ctypes.data))
+        return out
+
+    def report_n(self, index, loss):
+        """Reports loss[i] for pool index index[i], in one call."""
+        idx = np.ascontiguousarray(index, dtype=np.int32)
+        ls = np.ascontiguousarray(loss, dtype=np.float64)
+        if idx.size != ls.size:
+            raise ValueError("index and loss differ in length")
+        _check("cgs_sched_report_n", lib().cgs_sched_report_n(self._h, idx.ctypes.data, ls.ctypes.data, idx.size))
 
     def state(self):
         k = lib().cgs_sched_state(self._h, None, None, None, 0)

@@ -88,6 +88,27 @@ int cgs_sched_report(cgs_scheduler *s, int32_t index, double loss)
     return CGS_OK;
 }
 
+int cgs_sched_draw_n(cgs_scheduler *s, const uint32_t *rand_u32, int32_t n, int32_t *out)
+{
+    if (!s || n < 0 || (n > 0 && (!rand_u32 || !out))) return CGS_ERR_ARG;
+    for (int32_t i = 0; i < n; i++) {
+        const int rc = cgs_sched_draw(s, rand_u32[i]);
+        if (rc < 0) return rc;
+        out[i] = rc;
+    }
+    return CGS_OK;
+}
+
+int cgs_sched_report_n(cgs_scheduler *s, const int32_t *index, const double *loss, int32_t n)
+{
+    if (!s || n < 0 || (n > 0 && (!index || !loss))) return CGS_ERR_ARG;
+    for (int32_t i = 0; i < n; i++) {
+        const int rc = cgs_sched_report(s, index[i], loss[i]);
+        if (rc != CGS_OK) return rc;
+    }
+    return CGS_OK;
+}
+
 int cgs_sched_state(const cgs_scheduler *s, int32_t *ids, int32_t *r, double *l, int32_t cap)
 {
     if (!s) return CGS_ERR_ARG;

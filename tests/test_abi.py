@@ -89,3 +89,27 @@ def test_scheduler_matches_oracle(native):
         orc_s.report(b, loss)
         ids, r, l = lib_s.state()
         assert r == orc_s.R
+
+
+def test_scheduler_batched_calls_match_single_calls(native):
+    """cgs_sched_draw_n / cgs_sched_report_n act exactly as the same single calls in a row."""
+    import numpy as np
+    rng = np.random.default_rng(5)
+    a, b = native.Scheduler(4), native.Scheduler(4)
+    for k in range(16):
+        a.add(k, 8 if k % 2 else 2)
+        b.add(k, 8 if k % 2 else 2)
+    for _ in range(60):
+        u = rng.integers(0, 2 ** 32, 16, dtype=np.uint64).astype(np.uint32)
+        ia = a.draw_n(u)
+        ib = np.array([b.draw(int(x)) for x in u], dtype=np.int32)
+        assert np.array_equal(ia, ib)
+        loss = rng.uniform(0, 1, 16)
+        a.report_n(ia, loss)
+        for i, l in zip(ib, loss):
+            b.report(int(i), float(l))
+        assert a.state() == b.state()
+    assert a.draw_n(np.zeros(0, np.uint32)).size == 0
+    with pytest.raises(native.CgsError):
+        a.report_n([99], [0.5])
+
