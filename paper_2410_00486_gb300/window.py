@@ -106,7 +106,8 @@ class MappingWindow:
         self.denom = torch.zeros(self.n, **f32)
         self.max_r2d = torch.zeros(self.n, **f32)
         self._pv = None
-        self.graph = None
+        self._graphs = {}
+        self._set = 0   # which of the two input sets (staging swaps them) is current
         self._alloc_capacity(capacity if capacity else max(1 << 20, 16 * slots))
 
     # ------------------------------------------------------------ buffers
@@ -122,7 +123,7 @@ class MappingWindow:
             self.ckpt = torch.empty(nb // 4, dtype=torch.float32, device=self.device)
             self.bucket_start = _u32(self.Ttot + 1, self.device)
         self._pv = None
-        self.graph = None
+        self._graphs = {}
 
     def set_window(self, cams, tgt_rgb, tgt_depth=None, view_weight=None, non_blocking=True):
         """Copy the window's cameras (float32[V][20]), targets and view weights into the
@@ -164,14 +165,15 @@ class MappingWindow:
             self._staged.record(self._copy_stream)
 
     def commit_window(self):
-        """Make the staged inputs current: the compute stream waits for the staging copy, then
-        copies device to device into the buffers the iteration (and a captured graph) reads."""
+        """Make the staged inputs current: the compute stream waits for the staging copy and
+        the staging buffers become the window's inputs (no copy); the buffers they replace
+        take the next staging once the iterations already queued have read them.  Each of the
+        two input sets has its own captured graph (`replay`)."""
         cur = torch.cuda.current_stream(self.device)
         cur.wait_event(self._staged)
-        c, r, d = self._stage
-        self.cams.copy_(c)
-        self.tgt_rgb.copy_(r)
-        self.tgt_depth.copy_(d)
+        (self.cams, self.tgt_rgb, self.tgt_depth), self._stage = self._stage, (self.cams, self.tgt_rgb,
+                                                                              self.tgt_depth)
+        self._set ^= 1
         self._consumed.record(cur)
 
     # ---------------------------------------------------------- iteration
@@ -303,7 +305,7 @@ class MappingWindow:
         self.max_r2d = torch.zeros(self.n, **f32)
         self._alloc_capacity(self.capacity)    # the binning workspace depends on n
         self._pv = None
-        self.graph = None
+        self._graphs = {}
 
     # ------------------------------------------------------- per-view form
     def _per_view_buffers(self):
@@ -351,23 +353,38 @@ class MappingWindow:
 
     # --------------------------------------------------------- CUDA graph
     def capture(self, warmup: int = 0):
-        """Record one batched iteration (`step`) into a CUDA graph."""
+        """Record one batched iteration (`step`) into a CUDA graph for the current input
+        buffers (the graph of the other input set, after `commit_window`, is recorded at its
+        first `replay`)."""
         s = torch.cuda.Stream(device=self.device)
         s.wait_stream(torch.cuda.current_stream(self.device))
         with torch.cuda.stream(s):
             for _ in range(warmup):
                 self.step()
         torch.cuda.current_stream(self.device).wait_stream(s)
+        self._graphs = {}
+        return self._capture_current()
+
+    def _capture_current(self):
+        torch.cuda.synchronize(self.device)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             self.step()
-        self.graph = g
+        self._graphs[self._set] = g
         return g
 
+    @property
+    def graph(self):
+        """The captured iteration for the current input buffers (None if not captured)."""
+        return self._graphs.get(self._set)
+
     def replay(self):
-        if self.graph is None:
-            raise RuntimeError("capture() first")
-        self.graph.replay()
+        g = self._graphs.get(self._set)
+        if g is None:
+            if not self._graphs:
+                raise RuntimeError("capture() first")
+            g = self._capture_current()   # first replay on the other input set
+        g.replay()
 
     # ------------------------------------------------------------- status
     def read_status(self) -> tuple[int, int]:
