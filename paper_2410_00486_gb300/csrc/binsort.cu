@@ -32,7 +32,9 @@ constexpr int kBigThreads = 1024;
 constexpr int kBigCap = 16384;       // keys held in shared memory by the big-tile kernel
 constexpr uint64_t kPadKey = ~0ull;  // larger than any real key
 constexpr size_t kAggMaxSmem = 96 * 1024;   // per-view tile histogram in shared memory
-constexpr int kChunk = 4096;                // slots of a view per block of the count and scatter passes
+// Slots of a view per block of the count and scatter passes: 8192 measured 1% faster on the
+// 16-view window but 9% slower for one view at a time (half the blocks).
+constexpr int kChunk = 4096;
 
 struct BinWs {
     uint32_t *count;     // [Ttot + 1]
