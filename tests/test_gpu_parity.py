@@ -9,6 +9,8 @@ where the oracle finds a decision input (alpha vs 1/255 or 0.99, T vs 1e-4) with
 a relative 1e-5 of its threshold are excluded from the pixel check and counted
 (float32 and float64 may legitimately decide differently there).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -25,6 +27,8 @@ SCENES = {
     "tiny_sh3_3views": lambda: make_tiny_scene(seed=3, n=80, sh_degree=3, W=52, H=37, views=3, tile=8),
     "room_sh3_20k": lambda: make_scene(2, n=20000),
     "path_sh3_3views": lambda: make_scene(4, n=20000, views=3),
+    # 32x32 tiles (ragged rows at 680): four backward warps and sixteen forward warps per tile
+    "room_t32": lambda: dataclasses.replace(make_scene(2, n=20000), tile=32),
 }
 _cache = {}
 
@@ -110,6 +114,8 @@ BIN_CASES = [
     (1, 6000, 64, 48, 16, 10),       # lists of 1k-2k: the block-per-tile kernel
     (1, 12000, 64, 48, 16, 10),      # lists of 2k-16k: the large-bucket kernel
     (1, 40000, 32, 32, 16, 6),       # lists > 16k: the in-place global sort
+    (1, 3000, 640, 480, 8, 120),     # rects far above 64 tiles: the scatter repeats the reach test
+    (2, 1500, 333, 250, 16, 90),     # mixed rect sizes around the 64-tile mask limit, ragged edges
 ]
 
 
@@ -255,7 +261,7 @@ def gpu_forward_from_rec(N, sc, rec, pre, tgt_rgb, tgt_d, batch_depth=64, bg=(0.
 
 
 @pytest.mark.parametrize("name,bd", [("cfg1", 64), ("cfg3", 32), ("tiny_sh3_3views", 256),
-                                     ("room_sh3_20k", 128), ("path_sh3_3views", 64)])
+                                     ("room_sh3_20k", 128), ("path_sh3_3views", 64), ("room_t32", 128)])
 def test_render_fwd_matches_oracle(name, bd):
     native()
     N = native()
@@ -327,7 +333,7 @@ def test_render_fwd_background_and_ragged_tiles():
 
 
 @pytest.mark.parametrize("name,bd", [("cfg1", 64), ("cfg3", 128), ("tiny_sh3_3views", 32),
-                                     ("room_sh3_20k", 64), ("path_sh3_3views", 256)])
+                                     ("room_sh3_20k", 64), ("path_sh3_3views", 256), ("room_t32", 64)])
 def test_raster_bwd_matches_oracle(name, bd):
     torch = torch_cuda()
     N = native()
