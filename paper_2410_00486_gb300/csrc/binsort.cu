@@ -675,7 +675,7 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
                      int num_sms, cudaStream_t s)
 {
     const int64_t Ttot = g.Tv * V;
-    BinWs w;
+    BinWs w{};
     ws_layout(capacity, Ttot, chunk_count_entries(n, V, g.Tv), (int64_t)V * n, &w, ws);
     const float4 *r4 = reinterpret_cast<const float4 *>(rec);
     cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (2 * (size_t)Ttot + 2), s);
