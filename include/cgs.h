@@ -235,7 +235,8 @@ int cgs_raster_bwd(const float *rec, const uint32_t *vals, const uint32_t *range
  * Results equal cgs_raster_bwd's up to float summation order.
  *   cgs_ckpt_bytes(max_buckets, cfg) = max_buckets * tile^2 * 20 bytes of checkpoints;
  *     a window needs sum over tiles of ceil(len / 32) buckets <= n_inst / 32 + tiles.
- *   cgs_render_fwd_ckpt: cgs_render_fwd plus the checkpoints.
+ *   cgs_render_fwd_ckpt: cgs_render_fwd plus the checkpoints (its workspace's count of
+ *     blended pairs is written as 0 whatever cfg->count_work says).
  *     ckpt          device out, 16-byte aligned, cgs_ckpt_bytes(max_buckets, cfg) bytes
  *     bucket_start  device out, uint32[V * tiles_per_view + 1]: first bucket of each tile
  *     more buckets than max_buckets set CGS_ERR_CAPACITY (checkpoints past it are dropped)
