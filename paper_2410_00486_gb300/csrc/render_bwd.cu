@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
             sslot[i] = slot;
         }
         __syncthreads();
-#pragma unroll 2
+#pragma unroll 1
         for (int j = nraw - 1; j >= 0; j--) {
             const uint32_t pos = (uint32_t)(bstart + j);   // list position of splat j
             const float4 q0 = s0[j];
