@@ -58,8 +58,8 @@ __device__ __forceinline__ void item_tile(const uint32_t *order, const Grid &g, 
     tx = t - ty * g.Tx;
 }
 
-// Pixels per thread in the raster kernels: a thread owns several vertically adjacent pixels,
-// so the staged splat is read from shared memory once for PPT pixels and the backward's
+// Pixels per thread in the raster kernels: a thread owns several pixels of one column, so
+// the staged splat is read from shared memory once for PPT pixels and the backward's
 // per-(warp, splat) reduction covers 32*PPT pixels.
 // The forward keeps two (its per-thread state is small and occupancy pays; four measured
 // slower), the backward eight: one warp per 16x16 tile, half the warp reductions per pixel
@@ -76,9 +76,9 @@ __host__ __device__ constexpr int ppt_for()
 
 // Tile row (0..B-1) of a thread's first pixel; its pixel p lies G p rows further down,
 // G = 32 / B the number of B-wide row groups a warp spans.  The warp's pixels with the
-// same p thus form a block of G adjacent rows (B = 16: rows 2p, 2p + 1 of the warp's
-// eight), so a splat that covers few rows leaves whole p-steps of the warp idle, where
-// rows p, p + 4 (consecutive rows per thread) would keep every p-step busy.
+// same p thus form a block of G adjacent rows (B = 16: rows 2p and 2p + 1 of the warp's
+// rows), so a splat that covers few rows leaves whole p-steps of the warp idle; with
+// consecutive rows per thread every p-step would hold rows spread over the warp's span.
 template <int B, int P>
 __device__ __forceinline__ int thread_row0()
 {
@@ -136,8 +136,9 @@ __device__ __forceinline__ float exp2_fast(float x)
     return y;
 }
 
-// Exponent of the projected Gaussian at a pixel from a staged splat, with explicit
-// roundings so every raster kernel computes the same bits:
+// Exponent of the projected Gaussian at a pixel from a staged splat (in base-2 units, the
+// staged terms carrying log2 e), with explicit roundings so every raster kernel computes
+// the same bits:
 //   power = (-A/2 dx) dx + dy ((-C/2) dy + (-B) dx),  dx = u - x, dy = v - y.
 // The dx terms are shared by the pixels of a column: power_x gives them once, and
 // power_at finishes a pixel with two fused multiply-adds.

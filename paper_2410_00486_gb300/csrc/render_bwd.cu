@@ -6,7 +6,10 @@
 // A tile's list holds only splats that can reach alpha >= 1/255 in it (the binning's
 // test), the same list the forward walked.  Each pixel recomputes alpha exactly as the
 // forward did (same rounding, same decisions) and its transmittance from the stored final T,
-// T_j = T_{j+1} / (1 - alpha_j), so no per-pixel splat list is kept.
+// T_j = T_{j+1} / (1 - alpha_j), so no per-pixel splat list is kept.  A thread blends its
+// pixels in pairs: when either pixel of a pair blends splat j, both run through the blend
+// (the other with alpha = 0, which leaves its state as it is), so the two dependency chains
+// interleave.
 //
 // With R_j the colour behind splat j normalised by the transmittance just after it,
 // R_last = bg and R_{j-1} = a_j c_j + (1 - a_j) R_j (depth alike, starting at 0),

@@ -1,11 +1,12 @@
 // Forward blend of Eq. 1 (Sec. III-B, CaRtGS) with the L1 loss fused in.
 //
-// One block per (view, tile), two vertically adjacent pixels per thread.  The tile's
-// depth-sorted list (only splats that can reach alpha >= 1/255 in the tile: the binning's
-// test) is consumed in batches of BD splats: the block gathers the records of a batch
-// (48 bytes each, one per thread) into shared memory; every pixel then walks the batch
-// front to back, rejecting a pair on its exponent (power < tau) before any exponential.  A block-wide vote (__syncthreads_count) ends the walk as soon as every
-// pixel of the tile is saturated (T below 1e-4).
+// One block per (view, tile), two pixels of one column per thread (32/B rows apart).  The
+// tile's depth-sorted list (only splats that can reach alpha >= 1/255 in the tile: the
+// binning's test) is consumed in batches of BD splats: the block gathers the records of a
+// batch (48 bytes each, one per thread) into shared memory; every pixel then walks the
+// batch front to back, rejecting a pair on its base-2 exponent (power < tau, both scaled
+// by log2 e) before any exponential.  A block-wide vote (__syncthreads_count) ends the walk
+// as soon as every pixel of the tile is saturated (T below 1e-4).
 #include "raster.cuh"
 
 namespace cgs {
@@ -31,7 +32,6 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
     const int py0 = ty * B + row0;   // row of pixel p: py0 + G p
     const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
     const float fx = (float)px;
-    // pixel-centre box of the tile (clipped to the image)
 
     float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
     uint32_t lst[PPT];
