@@ -169,6 +169,8 @@ class MappingWindow:
         the staging buffers become the window's inputs (no copy); the buffers they replace
         take the next staging once the iterations already queued have read them.  Each of the
         two input sets has its own captured graph (`replay`)."""
+        if not hasattr(self, "_stage"):
+            raise RuntimeError("stage_window() first")
         cur = torch.cuda.current_stream(self.device)
         cur.wait_event(self._staged)
         (self.cams, self.tgt_rgb, self.tgt_depth), self._stage = self._stage, (self.cams, self.tgt_rgb,
