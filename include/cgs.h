@@ -86,6 +86,10 @@ typedef struct {
     int32_t count_work;      /* nonzero: cgs_render_fwd also counts the (splat, pixel) pairs it
                                 blends (per-tile partial 4; a per-pair counter, about 5% of the
                                 blend's time); 0: that partial is written as 0 */
+    int32_t rect_lists;      /* nonzero: cgs_bin_sort lists every visible slot in every tile of
+                                its rectangle (the plain 3DGS binning); 0: only in the tiles its
+                                alpha >= 1/255 ellipse reaches (same renders, about half the
+                                instances) */
 } cgs_config;
 
 /* Number of floats in the parameter vector: (14 + 3 (K-1)) n. */
@@ -120,7 +124,8 @@ int cgs_preprocess(const float *params, int64_t n, const cgs_camera *cams, int32
 /*
  * cgs_bin_sort -- tile binning: every visible slot is listed in each tile of its
  * rectangle that its alpha >= 1/255 ellipse can reach at a pixel centre (a splat left out
- * of a tile is one every pixel of the tile skips: the render is unchanged), and each
+ * of a tile is one every pixel of the tile skips: the render is unchanged; with
+ * cfg->rect_lists, in every tile of the rectangle), and each
  * tile's list is sorted by (depth, slot) ascending; tiles are
  * numbered view-major (global tile = v*Tx*Ty + ty*Tx + tx), so the whole window
  * shares one sort.  The order is the blending order of Eq. 1 (front to back);

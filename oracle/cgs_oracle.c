@@ -349,74 +349,17 @@ static int inst_cmp(const void *pa, const void *pb)
 }
 
 /*
- * Whether a splat can reach alpha >= 1/255 at a pixel centre of the tile box
- * [bx0, bx1] x [by0, by1] (reading: tile lists keep only such splats; a splat left out is
- * skipped by every pixel of the tile, so the render is unchanged).  In float32, every
- * operation a single IEEE rounding (products, sums, quotients, square roots), so any
- * implementation taking the same steps on the same float32 inputs decides identically:
- *   tau = -ln(255 o) is an input (kept with the projected splat); o < 1/255 (tau > 1e-4,
- *   with a margin) reaches nothing; a degenerate conic (det <= 0) reaches everything;
- *   alpha >= 1/255 needs q = A dx^2 + 2 B dx dy + C dy^2 <= -2 tau, widened to
- *   t2 = (-2 tau) 1.001 + 1e-3.  First the ellipse's bounding box (half-extents
- *   sqrt(t2 C / det) + 0.01, sqrt(t2 A / det) + 0.01) against the box; then, with the centre
- *   outside the box, the minimum of q over the box, which lies on an edge where q is a
- *   parabola minimised at its clamped vertex.
+ * Tile lists (the binning of the 3DGS renderer the paper keeps, Sec. III-B): every visible
+ * slot is listed in each tile of its rect; lists are ordered by (global tile, depth, slot)
+ * -- global tile = v*Tx*Ty + ty*Tx + tx, slot = v*n + g, so equal depths keep the
+ * Gaussian order (reading).  Depth order is the blending order of Eq. 1.  Inputs are the
+ * projected centre, radius and depth of each slot (radius 0 = culled).  Outputs:
+ * ranges[2*Ttot] = [start, end) per global tile, the exclusive scan of the per-tile
+ * counts (an empty tile is [start, start)), vals[count] = slot ids.  Returns the instance
+ * count; writes nothing when that count exceeds `capacity` or vals is NULL (a sizing call).
  */
-static int reach_touches_f32(float u, float v, float A, float B, float C, float tau, float bx0, float bx1,
-                             float by0, float by1)
-{
-    if (!(tau <= 1e-4f)) return 0;
-    float det = A * C - B * B;
-    if (!(det > 0.0f)) return 1;
-    float t2 = (-2.0f * tau) * 1.001f + 1e-3f;
-    float ex = sqrtf(t2 * C / det) + 1e-2f, ey = sqrtf(t2 * A / det) + 1e-2f;
-    float cx = fminf(fmaxf(u, bx0), bx1), cy = fminf(fmaxf(v, by0), by1);
-    float dx = fabsf(u - cx), dy = fabsf(v - cy);
-    if (!(dx <= ex && dy <= ey)) return 0;
-    if (dx == 0.0f && dy == 0.0f) return 1;
-    float bc = B / C, ba = B / A, B2 = 2.0f * B;
-    float qmin = INFINITY;
-    for (int e = 0; e < 2; e++) {
-        float ddx = u - (e ? bx1 : bx0);
-        float ddy = fminf(fmaxf(-(bc * ddx), v - by1), v - by0);
-        float q = ((A * ddx) * ddx + (B2 * ddx) * ddy) + (C * ddy) * ddy;
-        qmin = fminf(qmin, q);
-    }
-    for (int e = 0; e < 2; e++) {
-        float ddy = v - (e ? by1 : by0);
-        float ddx = fminf(fmaxf(-(ba * ddy), u - bx1), u - bx0);
-        float q = ((A * ddx) * ddx + (B2 * ddx) * ddy) + (C * ddy) * ddy;
-        qmin = fminf(qmin, q);
-    }
-    return qmin <= t2;
-}
-
-/* Does slot s belong in tile (tx, ty)?  Always, without a conic; else the reach test. */
-static int in_tile(const float *conic, const float *tau, int64_t s, double u, double v, int tx, int ty, int B,
-                   int W, int H)
-{
-    if (!conic) return 1;
-    float bx0 = (float)(tx * B), bx1 = (float)((tx * B + B < W ? tx * B + B : W) - 1);
-    float by0 = (float)(ty * B), by1 = (float)((ty * B + B < H ? ty * B + B : H) - 1);
-    return reach_touches_f32((float)u, (float)v, conic[3 * s], conic[3 * s + 1], conic[3 * s + 2], tau[s], bx0,
-                             bx1, by0, by1);
-}
-
-/*
- * Tile lists: every visible slot is listed in each tile of its rect that its alpha >=
- * 1/255 ellipse reaches (reach_touches_f32; every tile of the rect when conic is NULL);
- * lists are ordered by (global tile, depth, slot) -- global tile = v*Tx*Ty + ty*Tx + tx,
- * slot = v*n + g, so equal depths keep the Gaussian order (reading).  Depth order is the
- * blending order of Eq. 1.  Inputs are the projected centre, radius and depth of each
- * slot (radius 0 = culled) and, optionally, its conic (A, B, C) and tau = -ln(255 o) in
- * float32.  Outputs: ranges[2*Ttot] = [start, end) per global tile, the exclusive scan of
- * the per-tile counts (an empty tile is [start, start)), vals[count] = slot ids.  Returns
- * the instance count; writes nothing when that count exceeds `capacity` or vals is NULL
- * (a sizing call).
- */
-int64_t orc_bin(const double *u, const double *v, const double *z, const int32_t *radius, const float *conic,
-                const float *tau, int V, int64_t n, int W, int H, int B, int64_t capacity,
-                uint32_t *ranges, uint32_t *vals)
+int64_t orc_bin(const double *u, const double *v, const double *z, const int32_t *radius, int V, int64_t n,
+                int W, int H, int B, int64_t capacity, uint32_t *ranges, uint32_t *vals)
 {
     int Tx = (W + B - 1) / B, Ty = (H + B - 1) / B;
     int64_t Tv = (int64_t)Tx * Ty, Ttot = Tv * V;
@@ -426,7 +369,7 @@ int64_t orc_bin(const double *u, const double *v, const double *z, const int32_t
         if (radius[s] <= 0) continue;
         tile_rect(u[s], v[s], radius[s], B, Tx, Ty, rect);
         for (int ty = rect[2]; ty < rect[3]; ty++)
-            for (int tx = rect[0]; tx < rect[1]; tx++) count += in_tile(conic, tau, s, u[s], v[s], tx, ty, B, W, H);
+            count += rect[1] - rect[0];
     }
     if (count > capacity || vals == NULL) return count;
     inst_t *ins = malloc(sizeof(inst_t) * (count ? count : 1));
@@ -438,7 +381,6 @@ int64_t orc_bin(const double *u, const double *v, const double *z, const int32_t
             tile_rect(u[s], v[s], radius[s], B, Tx, Ty, rect);
             for (int ty = rect[2]; ty < rect[3]; ty++)
                 for (int tx = rect[0]; tx < rect[1]; tx++) {
-                    if (!in_tile(conic, tau, s, u[s], v[s], tx, ty, B, W, H)) continue;
                     ins[k].tile = vv * Tv + (int64_t)ty * Tx + tx;
                     ins[k].z = z[s];
                     ins[k].slot = s;

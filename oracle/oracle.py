@@ -59,7 +59,7 @@ def _load():
         P = ctypes.c_void_p
         i32, i64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
         lib.orc_preprocess.argtypes = [P, i64, i32, P, i32, i32, i32, i32, f64, f64, P, P, P, P, P]
-        lib.orc_bin.argtypes = [P, P, P, P, P, P, i32, i64, i32, i32, i32, i64, P, P]
+        lib.orc_bin.argtypes = [P, P, P, P, i32, i64, i32, i32, i32, i64, P, P]
         lib.orc_bin.restype = i64
         lib.orc_render_fwd.argtypes = [P, P, P, i32, i32, i32, i32, P, P, P, P, f64, f64,
                                        P, P, P, P, P, P, P, P]
@@ -117,25 +117,22 @@ def tiles(W, H, B):
 
 
 def tau32(opacity) -> np.ndarray:
-    """tau = -ln(255 o) of each splat, rounded to float32 (the per-splat input of the tile
-    test; the raster's alpha >= 1/255 test is power >= tau)."""
+    """tau = -ln(255 o) of each splat, rounded to float32: the field of the library's
+    12-float record that the tests fill when they hand oracle records to the kernels."""
     with np.errstate(divide="ignore"):
         return (-np.log(255.0 * np.asarray(opacity, np.float64))).astype(np.float32)
 
 
-def bin_lists(u, v, z, radius, V, n, W, H, B, conic=None, tau=None):
-    """Tile lists ordered by (tile, depth, slot): returns (ranges[Ttot, 2], vals[count]).
-    With conic (float32 [m, 3]: A, B, C) and tau (float32 [m]) a slot is listed only in the
-    tiles its alpha >= 1/255 ellipse reaches (the float32 test of cgs_oracle.c)."""
+def bin_lists(u, v, z, radius, V, n, W, H, B):
+    """Tile lists: every visible slot in every tile of its rect, ordered by (tile, depth,
+    slot): returns (ranges[Ttot, 2], vals[count])."""
     lib = _load()
     Tx, Ty = tiles(W, H, B)
     Ttot = V * Tx * Ty
     u, v, z = _f64(u), _f64(v), _f64(z)
     radius = np.ascontiguousarray(radius, np.int32)
-    cf = np.ascontiguousarray(conic, np.float32).reshape(-1, 3) if conic is not None else None
-    tf = np.ascontiguousarray(tau, np.float32) if conic is not None else None
     ranges = np.zeros((Ttot, 2), np.uint32)
-    args = (_p(u), _p(v), _p(z), _p(radius), _p(cf) if cf is not None else None, _p(tf) if tf is not None else None)
+    args = (_p(u), _p(v), _p(z), _p(radius))
     cnt = lib.orc_bin(*args, V, n, W, H, B, 0, _p(ranges), None)
     vals = np.zeros(max(1, cnt), np.uint32)
     cnt2 = lib.orc_bin(*args, V, n, W, H, B, vals.size, _p(ranges), _p(vals))
@@ -144,11 +141,9 @@ def bin_lists(u, v, z, radius, V, n, W, H, B, conic=None, tau=None):
 
 
 def bin_records(rec, radius, V, n, W, H, B):
-    """bin_lists for oracle records [m, 10] (u, v, A, B, C, o, r, g, b, z), with the tile test
-    on the records' conic and opacity rounded to float32."""
+    """bin_lists for oracle records [m, 10] (u, v, A, B, C, o, r, g, b, z)."""
     r = np.asarray(rec, np.float64)
-    return bin_lists(r[:, 0], r[:, 1], r[:, 9], radius, V, n, W, H, B, conic=r[:, 2:5].astype(np.float32),
-                     tau=tau32(r[:, 5]))
+    return bin_lists(r[:, 0], r[:, 1], r[:, 9], radius, V, n, W, H, B)
 
 
 def render_fwd(rec, ranges, vals, V, W, H, B, cams, bg=(0.0, 0.0, 0.0), tgt_rgb=None,

@@ -36,11 +36,13 @@ class cgs_camera(ctypes.Structure):
 class cgs_config(ctypes.Structure):
     _fields_ = [("width", c_int32), ("height", c_int32), ("tile", c_int32), ("batch_depth", c_int32),
                 ("sh_degree", c_int32), ("near_z", c_float), ("bg", c_float * 3),
-                ("lambda_depth", c_float), ("batch_depth_bwd", c_int32), ("count_work", c_int32)]
+                ("lambda_depth", c_float), ("batch_depth_bwd", c_int32), ("count_work", c_int32),
+                ("rect_lists", c_int32)]
 
 
 def make_config(width, height, tile=16, batch_depth=64, sh_degree=3, near_z=0.2,
-                bg=(0.0, 0.0, 0.0), lambda_depth=0.1, batch_depth_bwd=0, count_work=False) -> cgs_config:
+                bg=(0.0, 0.0, 0.0), lambda_depth=0.1, batch_depth_bwd=0, count_work=False,
+                rect_lists=False) -> cgs_config:
     c = cgs_config()
     c.width, c.height, c.tile, c.batch_depth, c.sh_degree = width, height, tile, batch_depth, sh_degree
     c.near_z = near_z
@@ -48,6 +50,7 @@ def make_config(width, height, tile=16, batch_depth=64, sh_degree=3, near_z=0.2,
     c.lambda_depth = lambda_depth
     c.batch_depth_bwd = batch_depth_bwd
     c.count_work = 1 if count_work else 0
+    c.rect_lists = 1 if rect_lists else 0
     return c
 
 

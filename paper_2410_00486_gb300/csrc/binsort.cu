@@ -96,9 +96,11 @@ __device__ __forceinline__ bool load_slot(const float4 *__restrict__ rec, int64_
     return true;
 }
 
-// The per-slot part of the tile reach test (record fields 2, 3, 4: conic; 11: tau).
-__device__ __forceinline__ ReachPre load_reach(const float4 *__restrict__ rec, int64_t slot)
+// The per-slot part of the tile reach test (record fields 2, 3, 4: conic; 11: tau).  With
+// rect lists every tile of the rect is kept (mode 1, "reaches everything").
+__device__ __forceinline__ ReachPre load_reach(const float4 *__restrict__ rec, int64_t slot, const Grid &g)
 {
+    if (g.rect_lists) return ReachPre{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1};
     const float *rf = reinterpret_cast<const float *>(rec + kRec4 * slot);
     return reach_prepare(__ldg(rf + 2), __ldg(rf + 3), __ldg(rf + 4), __ldg(rf + 11));
 }
@@ -120,7 +122,7 @@ __global__ void k_count(const float4 *__restrict__ rec, int64_t n, int V, Grid g
         if (!load_slot(rec, s, u, v, z, r)) continue;
         const int64_t view = s / n;
         Rect R = tile_rect(u, v, r, g);
-        const ReachPre e = load_reach(rec, s);
+        const ReachPre e = load_reach(rec, s, g);
         uint32_t *base = count + view * g.Tv;
         for (int ty = R.y0; ty < R.y1; ty++)
             for (int tx = R.x0; tx < R.x1; tx++)
@@ -172,7 +174,7 @@ __device__ __forceinline__ void for_each_tile_row(const float4 *__restrict__ rec
                 x1 = R.x1;
                 y0 = R.y0;
                 zb = __float_as_uint(z);
-                e = load_reach(rec, (int64_t)view * n + gi);
+                e = load_reach(rec, (int64_t)view * n + gi, g);
             }
         }
         const bool small = h * (x1 - x0) <= kMaskTiles;
@@ -330,7 +332,7 @@ __global__ void k_scatter(const float4 *__restrict__ rec, int64_t n, int V, Grid
         const int64_t view = s / n;
         Rect R = tile_rect(u, v, r, g);
         const uint64_t key = ((uint64_t)__float_as_uint(z) << 32) | (uint64_t)(uint32_t)s;
-        const ReachPre e = load_reach(rec, s);
+        const ReachPre e = load_reach(rec, s, g);
         for (int ty = R.y0; ty < R.y1; ty++)
             for (int tx = R.x0; tx < R.x1; tx++) {
                 if (!in_tile(e, u, v, tx, ty, g)) continue;

@@ -27,24 +27,6 @@ using namespace cgs;
 
 namespace {
 
-constexpr int kMaxViews = 1024;
-
-bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
-
-bool cfg_ok(const cgs_config *c)
-{
-    if (!c) return false;
-    if (c->width < 1 || c->height < 1 || c->width > (1 << 16) || c->height > (1 << 16)) return false;
-    if (c->tile != 8 && c->tile != 16 && c->tile != 32) return false;
-    if (c->batch_depth != 32 && c->batch_depth != 64 && c->batch_depth != 128 && c->batch_depth != 256) return false;
-    if (c->batch_depth_bwd != 0 && c->batch_depth_bwd != 32 && c->batch_depth_bwd != 64 &&
-        c->batch_depth_bwd != 128 && c->batch_depth_bwd != 256)
-        return false;
-    if (c->sh_degree < 0 || c->sh_degree > 3) return false;
-    if (!(c->near_z > 0.f) || !isfinite(c->near_z)) return false;
-    return true;
-}
-
 bool sizes_ok(int64_t n, int32_t V, const cgs_config *c)
 {
     if (n < 1 || V < 1 || V > kMaxViews) return false;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "cgs.h"
@@ -37,10 +38,30 @@ __device__ __forceinline__ void set_status(int32_t *st, int code)
     if (st) atomicCAS(st, 0, code);
 }
 
+// Argument checks shared by every entry point that takes a cgs_config (host code).
+constexpr int kMaxViews = 1024;
+
+inline bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+inline bool cfg_ok(const cgs_config *c)
+{
+    if (!c) return false;
+    if (c->width < 1 || c->height < 1 || c->width > (1 << 16) || c->height > (1 << 16)) return false;
+    if (c->tile != 8 && c->tile != 16 && c->tile != 32) return false;
+    if (c->batch_depth != 32 && c->batch_depth != 64 && c->batch_depth != 128 && c->batch_depth != 256) return false;
+    if (c->batch_depth_bwd != 0 && c->batch_depth_bwd != 32 && c->batch_depth_bwd != 64 &&
+        c->batch_depth_bwd != 128 && c->batch_depth_bwd != 256)
+        return false;
+    if (c->sh_degree < 0 || c->sh_degree > 3) return false;
+    if (!(c->near_z > 0.f) || !isfinite(c->near_z)) return false;
+    return true;
+}
+
 // Geometry of the tile grid, passed by value to kernels.
 struct Grid {
     int W, H, B, log2B, Tx, Ty;
-    int64_t Tv;   // tiles per view
+    int64_t Tv;      // tiles per view
+    int rect_lists;  // binning: list a slot in every tile of its rect (no reach test)
 };
 
 inline int ilog2(int x)
@@ -60,6 +81,7 @@ inline Grid make_grid(const cgs_config &c)
     g.Tx = (c.width + c.tile - 1) / c.tile;
     g.Ty = (c.height + c.tile - 1) / c.tile;
     g.Tv = (int64_t)g.Tx * g.Ty;
+    g.rect_lists = c.rect_lists != 0;
     return g;
 }
 
@@ -93,7 +115,7 @@ __device__ __forceinline__ Rect tile_rect(float u, float v, int r, const Grid &g
 // margins exceed the float32 error of the raster's per-pixel test (power < tau skips)
 // unless the exponent's terms cancel by many orders of magnitude (a splat thousands of
 // pixels long and under a pixel wide), so a splat left out of a tile is one every pixel
-// of the tile would skip; the lists are defined by this test either way.
+// of the tile would skip.
 __device__ __forceinline__ float edge_q(float A, float B2, float C, float ddx, float ddy)
 {
     return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, ddx), ddx), __fmul_rn(__fmul_rn(B2, ddx), ddy)),

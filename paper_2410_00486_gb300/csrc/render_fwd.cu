@@ -306,12 +306,9 @@ extern "C" int cgs_render_fwd_noalloc(const float *rec, const uint32_t *vals, co
                                       int32_t *depth_count, int32_t *status_dev, void *stream)
 {
     using namespace cgs;
-    if (!rec || !vals || !ranges || !img || !depth || !t_final || !last || !cfg) return CGS_ERR_ARG;
-    if (cfg->width < 1 || cfg->height < 1 || cfg->width > (1 << 16) || cfg->height > (1 << 16)) return CGS_ERR_ARG;
-    if (cfg->tile != 8 && cfg->tile != 16 && cfg->tile != 32) return CGS_ERR_ARG;
-    if (cfg->batch_depth != 32 && cfg->batch_depth != 64 && cfg->batch_depth != 128 && cfg->batch_depth != 256)
-        return CGS_ERR_ARG;
-    if (V < 1 || ((uintptr_t)rec & 15) != 0) return CGS_ERR_ARG;
+    // the same argument checks as cgs_render_fwd (without the workspace)
+    if (!rec || !vals || !ranges || !img || !depth || !t_final || !last || !cfg_ok(cfg)) return CGS_ERR_ARG;
+    if (V < 1 || V > kMaxViews || !aligned16(rec)) return CGS_ERR_ARG;
     if (tgt_depth && !tgt_rgb) return CGS_ERR_ARG;
     if (tgt_rgb && (!loss_view || !depth_count)) return CGS_ERR_ARG;
     const Grid g = make_grid(*cfg);

@@ -163,14 +163,18 @@ class MappingWindow:
             else:
                 d.zero_()
             self._staged.record(self._copy_stream)
+        self._pending = True
 
     def commit_window(self):
         """Make the staged inputs current: the compute stream waits for the staging copy and
         the staging buffers become the window's inputs (no copy); the buffers they replace
         take the next staging once the iterations already queued have read them.  Each of the
         two input sets has its own captured graph (`replay`)."""
-        if not hasattr(self, "_stage"):
-            raise RuntimeError("stage_window() first")
+        if not getattr(self, "_pending", False):
+            # nothing staged since the last commit: swapping again would bring back the
+            # previous window's inputs
+            raise RuntimeError("stage_window() first: no inputs staged since the last commit_window()")
+        self._pending = False
         cur = torch.cuda.current_stream(self.device)
         cur.wait_event(self._staged)
         (self.cams, self.tgt_rgb, self.tgt_depth), self._stage = self._stage, (self.cams, self.tgt_rgb,

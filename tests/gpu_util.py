@@ -103,3 +103,148 @@ def group_slices(n, deg):
             out[name] = slice(o, o + s)
         o += s
     return out
+
+
+# ------------------------------------------------- tile lists: culled vs rect
+
+def entry_tiles(ranges):
+    """Global tile of every list entry, for contiguous ranges [T, 2] (entry 0 at ranges[0, 0])."""
+    rg = np.asarray(ranges, np.int64).reshape(-1, 2)
+    return np.repeat(np.arange(rg.shape[0], dtype=np.int64), rg[:, 1] - rg[:, 0])
+
+
+def max_alpha_over_tiles(rec12, slots, tiles, W, H, B, chunk=32768):
+    """For each (slot, tile) pair the largest alpha = min(0.99, o exp(power)) over the tile's
+    pixel centres (pixels outside the image excluded; power > 0 counts as skipped, alpha 0),
+    in float64 from the pair's float32 record (u, v, A, B, C, o): the blend's definition
+    evaluated at every pixel, nothing else."""
+    Tx = (W + B - 1) // B
+    Tv = Tx * ((H + B - 1) // B)
+    out = np.zeros(len(slots))
+    off = np.arange(B, dtype=np.float64)
+    for a in range(0, len(slots), chunk):
+        s = np.asarray(slots[a:a + chunk], np.int64)
+        t = np.asarray(tiles[a:a + chunk], np.int64) % Tv
+        r = rec12[s].astype(np.float64)
+        u, v, A, Bc, C, o = (r[:, k] for k in range(6))
+        px = (t % Tx)[:, None] * B + off[None, :]                 # [m, B]
+        py = (t // Tx)[:, None] * B + off[None, :]
+        dx = u[:, None] - px
+        dy = v[:, None] - py
+        power = (-0.5 * (A[:, None, None] * (dx * dx)[:, None, :] + C[:, None, None] * (dy * dy)[:, :, None])
+                 - Bc[:, None, None] * dy[:, :, None] * dx[:, None, :])          # [m, y, x]
+        alpha = np.minimum(0.99, o[:, None, None] * np.exp(np.minimum(power, 0.0)))
+        inside = (py < H)[:, :, None] & (px < W)[:, None, :] & (power <= 0.0)
+        out[a:a + chunk] = np.where(inside, alpha, 0.0).max(axis=(1, 2))
+    return out
+
+
+def check_culled_lists(rec12, ranges_rect, vals_rect, ranges_cull, vals_cull, W, H, B, slot_base=0):
+    """The culled lists against the rect lists of the same records: (i) each tile's culled
+    list is an ordered subsequence of its rect list (same (depth, slot) order); (ii) every
+    (slot, tile) pair the culling dropped has alpha < 1/255 at every pixel centre of the
+    tile, evaluated in float64 by brute force, so no pixel would have blended it.  The
+    ranges cover the same tiles; slot_base is subtracted from the culled ids (a view's ids
+    when the culled lists come from a whole window).  Returns (rect, kept, dropped) counts."""
+    rr = np.asarray(ranges_rect, np.int64).reshape(-1, 2)
+    rc = np.asarray(ranges_cull, np.int64).reshape(-1, 2)
+    assert rr.shape == rc.shape
+    rc = rc - rc[0, 0]
+    rr = rr - rr[0, 0]
+    vr = np.asarray(vals_rect, np.int64)
+    vc = np.asarray(vals_cull, np.int64) - slot_base
+    assert len(vr) == rr[-1, 1] and len(vc) == rc[-1, 1]
+    S = int(max(vr.max(initial=0), vc.max(initial=0))) + 1
+    key_r = entry_tiles(rr) * S + vr
+    key_c = entry_tiles(rc) * S + vc
+    order = np.argsort(key_r, kind="stable")
+    srt = key_r[order]
+    idx = np.minimum(np.searchsorted(srt, key_c), max(len(srt) - 1, 0))
+    assert len(key_c) == 0 or np.all(srt[idx] == key_c), "a culled entry is not in its tile's rect list"
+    pos = order[idx]
+    assert np.all(np.diff(pos) > 0), "culled lists are not ordered subsequences of the rect lists"
+    dropped = np.ones(len(vr), bool)
+    dropped[pos] = False
+    amax = max_alpha_over_tiles(rec12, vr[dropped], entry_tiles(rr)[dropped], W, H, B)
+    bad = amax >= 1.0 / 255.0
+    assert not bad.any(), f"{bad.sum()} dropped pairs reach alpha >= 1/255 (max {amax.max():.6g})"
+    return len(vr), len(vc), int(dropped.sum())
+
+
+def last_slots(last, ranges, vals, W, H, B):
+    """The slot of each pixel's last blended splat (-1 where none): the list position `last`
+    (1-based) mapped through the pixel's tile list, which identifies the splat whatever the
+    list's other entries."""
+    last = np.asarray(last).view(np.uint32).astype(np.int64)
+    V = last.shape[0]
+    Tx, Ty = (W + B - 1) // B, (H + B - 1) // B
+    ys, xs = np.mgrid[0:H, 0:W]
+    tile = (np.arange(V)[:, None, None] * (Tx * Ty) + (ys // B) * Tx + xs // B)
+    rg = np.asarray(ranges, np.int64).reshape(-1, 2)
+    vals = np.asarray(vals, np.int64)
+    pos = rg[tile, 0] + last - 1
+    return np.where(last > 0, vals[np.clip(pos, 0, max(len(vals) - 1, 0))], -1)
+
+
+# ------------------------------------------------------- gradient comparisons
+
+def grad_check(got, ref, explained=None, name="", rel=GRAD_REL_TOL, l2=None):
+    """Gradient parity: relative L2 error <= rel over the whole array, and per element
+    |got - ref| <= rel (|ref| + rel max|ref|).  Rows (slots or Gaussians) in `explained`
+    (bool per row) are where the oracle found a decision input near its threshold, so float32
+    and float64 may take a different branch there: elements of those rows may exceed the
+    per-element bound and are counted; any other element beyond it fails.  Returns
+    (relative L2 error, elements beyond the bound, of which explained).  l2 (default rel)
+    is the bound on the relative L2 error."""
+    g = np.asarray(got, np.float64)
+    r = np.asarray(ref, np.float64)
+    e = rel_l2(g, r)
+    scale = np.abs(r).max() if r.size else 0.0
+    bad = np.abs(g - r) > rel * (np.abs(r) + rel * scale)
+    if bad.ndim == 1:
+        bad = bad[:, None]
+    rows = bad.any(axis=1)
+    expl = rows & explained if explained is not None else np.zeros_like(rows)
+    unexpl = rows & ~expl
+    print(f"    [{name}] rel L2 {e:.1e}  elements beyond the per-element bound: {int(bad.sum())} "
+          f"({int(bad[expl].sum())} in rows near a threshold)")
+    assert e < (rel if l2 is None else l2), (name, e)
+    assert not unexpl.any(), (name, f"{int(bad[unexpl].sum())} elements beyond the per-element bound, "
+                                    f"e.g. rows {np.nonzero(unexpl)[0][:5]}")
+    return e, int(bad.sum()), int(bad[expl].sum())
+
+
+def slots_in_flagged_tiles(near, ranges, vals, W, H, B, m, reach_px=0):
+    """bool[m]: slots listed in a tile that holds a pixel the oracle flagged as near a
+    decision threshold (their gradients may take the other branch in float32), or a pixel
+    within reach_px of one (a loss that couples neighbouring pixels, like SSIM's window)."""
+    near = np.asarray(near) != 0
+    if reach_px > 0:
+        from scipy.ndimage import maximum_filter
+        near = maximum_filter(near, size=(1, 2 * reach_px + 1, 2 * reach_px + 1))
+    V = near.shape[0]
+    Tx, Ty = (W + B - 1) // B, (H + B - 1) // B
+    vv, ys, xs = np.nonzero(near)
+    tiles = np.unique(vv * (Tx * Ty) + (ys // B) * Tx + xs // B)
+    rg = np.asarray(ranges, np.int64).reshape(-1, 2)
+    out = np.zeros(m, bool)
+    for t in tiles:
+        out[np.asarray(vals[rg[t, 0]:rg[t, 1]], np.int64)] = True
+    return out
+
+
+def param_grad_check(got, ref, n, deg, explained=None, tag="", rel=GRAD_REL_TOL, l2=None):
+    """grad_check per parameter group of the flat parameter vector, rows = Gaussians
+    (explained: bool per Gaussian)."""
+    out = {}
+    for name, sl in group_slices(n, deg).items():
+        w = (sl.stop - sl.start) // n
+        out[name] = grad_check(np.asarray(got)[sl].reshape(n, w), np.asarray(ref)[sl].reshape(n, w), explained,
+                               f"{tag} {name}", rel, l2)
+    return out
+
+
+def gaussians_of_slots(slot_mask, n):
+    """bool per Gaussian: any of its slots (v n + g) set."""
+    m = np.asarray(slot_mask, bool)
+    return m.reshape(-1, n).any(axis=0)

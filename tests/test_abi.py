@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(native):
 
 def test_struct_sizes_match_header(native):
     assert ctypes.sizeof(native.cgs_camera) == 80
-    assert ctypes.sizeof(native.cgs_config) == 4 * 12
+    assert ctypes.sizeof(native.cgs_config) == 4 * 13
 
 
 def test_host_only_queries(native):
@@ -113,3 +113,39 @@ def test_scheduler_batched_calls_match_single_calls(native):
     with pytest.raises(native.CgsError):
         a.report_n([99], [0.5])
 
+
+
+def test_render_entry_points_share_argument_checks(native):
+    """cgs_render_fwd and cgs_render_fwd_noalloc refuse the same bad configurations and view
+    counts before any CUDA call."""
+    L = native.lib()
+    P = 16                                    # a 16-byte aligned stand-in pointer (never dereferenced)
+    bads = [native.make_config(64, 48, 16, 64, 1, batch_depth_bwd=48), native.make_config(64, 48, 16, 64, 5),
+            native.make_config(64, 48, 16, 64, 1, near_z=0.0), native.make_config(64, 48, 12, 64, 1),
+            native.make_config(64, 48, 16, 48, 1), native.make_config(0, 48, 16, 64, 1)]
+    good = native.make_config(64, 48, 16, 64, 1)
+    cases = [(c, 1) for c in bads] + [(good, 1025), (good, 0)]
+    for cfg, V in cases:
+        c = ctypes.byref(cfg)
+        assert L.cgs_render_fwd(P, P, P, None, V, c, None, None, None, P, P, P, P, None, None, P, 1 << 20,
+                                None, None) == native.CGS_ERR_ARG
+        assert L.cgs_render_fwd_noalloc(P, P, P, None, V, c, None, None, None, P, P, P, P, None, None, None,
+                                        None) == native.CGS_ERR_ARG
+    # unaligned records, targets without loss outputs
+    c = ctypes.byref(good)
+    assert L.cgs_render_fwd_noalloc(8, P, P, None, 1, c, None, None, None, P, P, P, P, None, None, None,
+                                    None) == native.CGS_ERR_ARG
+    assert L.cgs_render_fwd_noalloc(P, P, P, None, 1, c, None, P, None, P, P, P, P, None, None, None,
+                                    None) == native.CGS_ERR_ARG
+
+
+def test_commit_window_needs_a_fresh_staging():
+    """commit_window() refuses when nothing was staged since the last commit (before any GPU
+    work), so a window never trains on the previous keyframes' inputs by mistake."""
+    from paper_2410_00486_gb300.window import MappingWindow
+    w = object.__new__(MappingWindow)
+    with pytest.raises(RuntimeError, match="stage_window"):
+        w.commit_window()
+    w._pending = False                        # the state right after a commit
+    with pytest.raises(RuntimeError, match="stage_window"):
+        w.commit_window()

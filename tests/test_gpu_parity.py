@@ -3,11 +3,16 @@ through the C ABI (GPU).  Sizes span several tiles and ragged tile tails; the
 workload-sized cases (the benchmark's window) live in test_gpu_fullsize.py.
 
 Tolerances: max |pixel| error 1e-4 (RGB, transmittance; depth relative to the
-scene's depth scale), gradient relative L2 error 1e-3 per parameter group; tile
-lists and orders bit-exact when both sides bin the same float32 records.  Pixels
-where the oracle finds a decision input (alpha vs 1/255 or 0.99, T vs 1e-4) within
-a relative 1e-5 of its threshold are excluded from the pixel check and counted
-(float32 and float64 may legitimately decide differently there).
+scene's depth scale); gradients: relative L2 error 1e-3 per parameter group or record
+field, and per element |g - g*| <= 1e-3 (|g*| + 1e-3 max|g*|).  Tile lists: with
+rect lists (every tile of a slot's rectangle) bit-exact with the oracle's; the default
+culled lists are checked against those: ordered subsequences whose every dropped
+(slot, tile) pair has alpha < 1/255 at all the tile's pixel centres (float64 brute
+force).  Pixels where the oracle finds a decision input (alpha vs 1/255 or 0.99, T vs
+1e-4) within a relative 1e-5 of its threshold are excluded from the pixel check and
+counted (float32 and float64 may legitimately decide differently there); gradient
+elements of slots listed in a tile holding such a pixel may exceed the per-element
+bound and are counted.
 """
 import dataclasses
 
@@ -16,8 +21,9 @@ import pytest
 
 from oracle import oracle as O
 from synth import make_conics, make_scene, make_tiny_scene, make_records
-from tests.gpu_util import (GRAD_REL_TOL, PIX_TOL, group_slices, native, oracle_targets, rec_from_gpu,
-                            rec_to_gpu, rel_l2, round32, sg_from_gpu, sg_to_gpu, torch_cuda)
+from tests.gpu_util import (GRAD_REL_TOL, PIX_TOL, check_culled_lists, gaussians_of_slots, grad_check,
+                            last_slots, native, oracle_targets, param_grad_check, rec_from_gpu, rec_to_gpu, rel_l2,
+                            round32, sg_from_gpu, sg_to_gpu, slots_in_flagged_tiles, torch_cuda)
 
 pytestmark = pytest.mark.gpu
 
@@ -41,8 +47,9 @@ def scene(name):
     return _cache[name]
 
 
-def cfg_for(N, sc, batch_depth=64, tile=None, bg=(0.0, 0.0, 0.0)):
-    return N.make_config(sc.width, sc.height, tile or sc.tile, batch_depth, sc.sh_degree, 0.2, bg, 0.1)
+def cfg_for(N, sc, batch_depth=64, tile=None, bg=(0.0, 0.0, 0.0), rect_lists=False):
+    return N.make_config(sc.width, sc.height, tile or sc.tile, batch_depth, sc.sh_degree, 0.2, bg, 0.1,
+                         rect_lists=rect_lists)
 
 
 def gpu_scene_tensors(sc):
@@ -90,6 +97,9 @@ def test_preprocess_matches_oracle(name):
           f"conic {(e[:, 2:5] / con_scale).max():.2e} rgb {e[:, 6:9].max():.2e}")
 
 
+FIELDS = ["u", "v", "A", "B", "C", "o", "r", "g", "b", "z"]
+
+
 # ---------------------------------------------------------------- bin sort
 
 def gpu_bin(N, rec_gpu, n, V, cfg, capacity, order=True):
@@ -119,32 +129,110 @@ BIN_CASES = [
 ]
 
 
-@pytest.mark.parametrize("case", BIN_CASES)
-def test_bin_sort_bit_exact(case):
-    torch = torch_cuda()
-    N = native()
+def bin_case_records(case, seed_off=0):
     V, n, W, H, B, maxr = case
-    u, v, r, z = make_records(17 + n, V, n, W, H, max_radius=maxr)
-    conic, opac = make_conics(18 + n, r)
+    u, v, r, z = make_records(17 + n + seed_off, V, n, W, H, max_radius=maxr)
+    conic, opac = make_conics(18 + n + seed_off, r)
     rec10 = np.zeros((V * n, 10))
     rec10[:, 0], rec10[:, 1], rec10[:, 9] = u, v, z
     rec10[:, 2:5], rec10[:, 5] = conic, opac
+    return rec10, r
+
+
+def gpu_lists(vals, ranges, cnt=None):
+    rg = ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
+    cnt = int(rg[-1, 1]) if cnt is None else cnt
+    return rg, vals.cpu().numpy().view(np.uint32)[:cnt]
+
+
+@pytest.mark.parametrize("case", BIN_CASES)
+def test_bin_sort_rect_lists_bit_exact(case):
+    """With rect lists the GPU binning lists every tile of each rect, and the lists, ranges and
+    instance count equal the oracle's bit for bit; the work order is a permutation by
+    non-increasing list length class."""
+    torch = torch_cuda()
+    N = native()
+    V, n, W, H, B, _ = case
+    rec10, r = bin_case_records(case)
     g = rec_to_gpu(rec10, r)
-    cfg = N.make_config(W, H, B, 64, 0)
-    ranges_o, vals_o = O.bin_lists(u, v, z, r, V, n, W, H, B, conic=conic, tau=O.tau32(opac))
+    cfg = N.make_config(W, H, B, 64, 0, rect_lists=True)
+    ranges_o, vals_o = O.bin_lists(rec10[:, 0], rec10[:, 1], rec10[:, 9], r, V, n, W, H, B)
     cnt = len(vals_o)
     vals, ranges, tord, ninst, st = gpu_bin(N, g, n, V, cfg, cnt + 7)
     assert st == 0 and ninst == cnt
-    rg = ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
+    rg, vv = gpu_lists(vals, ranges, cnt)
     assert np.array_equal(rg, ranges_o)
-    assert np.array_equal(vals.cpu().numpy().view(np.uint32)[:cnt], vals_o)
-    # work order: a permutation, by non-increasing floor(log2(length))
+    assert np.array_equal(vv, vals_o)
     to = tord.cpu().numpy()
     assert np.array_equal(np.sort(to), np.arange(len(rg)))
     lens = (rg[:, 1] - rg[:, 0]).astype(np.int64)[to]
     bucket = np.where(lens > 0, np.floor(np.log2(np.maximum(lens, 1))) + 1, 0)
     assert np.all(np.diff(bucket) <= 0)
-    print(f"[bin {case}] instances {cnt} longest list {lens.max()}")
+    print(f"[bin rect {case}] instances {cnt} longest list {lens.max()}")
+
+
+@pytest.mark.parametrize("case", BIN_CASES)
+def test_bin_sort_culled_lists_are_valid(case):
+    """The default binning lists a slot only in the tiles its alpha >= 1/255 ellipse reaches:
+    each tile's list is an ordered subsequence of the oracle's rect list, and every pair it
+    left out has alpha < 1/255 at every pixel centre of the tile (float64 brute force)."""
+    torch = torch_cuda()
+    N = native()
+    V, n, W, H, B, _ = case
+    rec10, r = bin_case_records(case)
+    g = rec_to_gpu(rec10, r)
+    cfg = N.make_config(W, H, B, 64, 0)
+    ranges_o, vals_o = O.bin_lists(rec10[:, 0], rec10[:, 1], rec10[:, 9], r, V, n, W, H, B)
+    vals, ranges, tord, ninst, st = gpu_bin(N, g, n, V, cfg, len(vals_o) + 7)
+    assert st == 0 and ninst <= len(vals_o)
+    rg, vv = gpu_lists(vals, ranges, ninst)
+    rec12 = g.cpu().numpy().reshape(-1, 12)
+    tot, kept, dropped = check_culled_lists(rec12, ranges_o, vals_o, rg, vv, W, H, B)
+    assert kept == ninst and dropped > 0
+    to = tord.cpu().numpy()
+    assert np.array_equal(np.sort(to), np.arange(len(rg)))
+    print(f"[bin culled {case}] rect {tot} kept {kept} dropped {dropped}")
+
+
+def test_bin_sort_thin_ellipses_at_the_rect_edge():
+    """Long thin splats (aspect up to 1:400, every orientation) centred near tile corners and
+    edges, with opacities just above 1/255 to 1: their rects hold many tiles the ellipse misses.
+    The culled lists stay valid against the rect lists, and some tiles are dropped."""
+    torch = torch_cuda()
+    N = native()
+    rng = np.random.default_rng(9)
+    W, H, B, n = 257, 131, 16, 3000
+    lmax = rng.uniform(20.0, 4000.0, n)
+    lmin = rng.uniform(0.01, 0.5, n)
+    th = rng.uniform(0, np.pi, n)
+    c, s_ = np.cos(th), np.sin(th)
+    sxx, syy, sxy = c * c * lmax + s_ * s_ * lmin, s_ * s_ * lmax + c * c * lmin, c * s_ * (lmax - lmin)
+    sxx, syy = sxx + 0.3, syy + 0.3
+    det = sxx * syy - sxy * sxy
+    conic = np.stack([syy / det, -sxy / det, sxx / det], 1).astype(np.float32)
+    u = (rng.integers(0, W // B + 1, n) * B + rng.choice([-0.5, 0.0, 0.49, 7.5], n)).astype(np.float32)
+    v = (rng.integers(0, H // B + 1, n) * B + rng.choice([-0.5, 0.0, 0.49, 7.5], n)).astype(np.float32)
+    mid = 0.5 * (sxx + syy)
+    r = np.ceil(3.0 * np.sqrt(mid + np.sqrt(np.maximum(0.1, mid * mid - det)))).astype(np.int32)
+    opac = np.where(rng.uniform(size=n) < 0.5, rng.uniform(1.0 / 255.0, 0.02, n), rng.uniform(0.02, 1.0, n))
+    z = rng.uniform(0.5, 20.0, n).astype(np.float32)
+    rec10 = np.zeros((n, 10))
+    rec10[:, 0], rec10[:, 1], rec10[:, 9] = u, v, z
+    rec10[:, 2:5], rec10[:, 5] = conic, opac
+    g = rec_to_gpu(rec10, r)
+    ranges_o, vals_o = O.bin_lists(rec10[:, 0], rec10[:, 1], rec10[:, 9], r, 1, n, W, H, B)
+    for rect in (True, False):
+        cfg = N.make_config(W, H, B, 64, 0, rect_lists=rect)
+        vals, ranges, _, ninst, st = gpu_bin(N, g, n, 1, cfg, len(vals_o) + 7)
+        assert st == 0
+        rg, vv = gpu_lists(vals, ranges, ninst)
+        if rect:
+            assert np.array_equal(rg, ranges_o) and np.array_equal(vv, vals_o)
+        else:
+            tot, kept, dropped = check_culled_lists(g.cpu().numpy().reshape(-1, 12), ranges_o, vals_o, rg, vv,
+                                                    W, H, B)
+            assert dropped > 0.5 * tot
+            print(f"[bin thin ellipses] rect {tot} kept {kept} dropped {dropped}")
 
 
 def test_bin_sort_depth_ties_bit_exact():
@@ -177,15 +265,19 @@ def test_bin_sort_depth_ties_bit_exact():
     rec10[:, 0], rec10[:, 1], rec10[:, 9] = u, v, z
     rec10[:, 2:5], rec10[:, 5] = conic, opac
     g = rec_to_gpu(rec10, r)
-    cfg = N.make_config(W, H, B, 64, 0)
-    ranges_o, vals_o = O.bin_lists(u, v, z.astype(np.float64), r, 1, n, W, H, B, conic=conic, tau=O.tau32(opac))
+    ranges_o, vals_o = O.bin_lists(u, v, z.astype(np.float64), r, 1, n, W, H, B)
     cnt = len(vals_o)
     lens = ranges_o[:, 1].astype(np.int64) - ranges_o[:, 0]
     assert lens.max() < 2048 and lens[0] > 100     # the block-per-tile kernel; tile 0 holds the run of 100
-    vals, ranges, _, ninst, st = gpu_bin(N, g, n, 1, cfg, cnt + 3)
-    assert st == 0 and ninst == cnt
-    assert np.array_equal(ranges.cpu().numpy().view(np.uint32).reshape(-1, 2), ranges_o)
-    assert np.array_equal(vals.cpu().numpy().view(np.uint32)[:cnt], vals_o)
+    for rect in (True, False):
+        cfg = N.make_config(W, H, B, 64, 0, rect_lists=rect)
+        vals, ranges, _, ninst, st = gpu_bin(N, g, n, 1, cfg, cnt + 3)
+        assert st == 0
+        rg, vv = gpu_lists(vals, ranges, ninst)
+        if rect:
+            assert ninst == cnt and np.array_equal(rg, ranges_o) and np.array_equal(vv, vals_o)
+        else:
+            check_culled_lists(g.cpu().numpy().reshape(-1, 12), ranges_o, vals_o, rg, vv, W, H, B)
 
 
 def test_bin_sort_capacity_overflow_reports_and_truncates():
@@ -198,8 +290,8 @@ def test_bin_sort_capacity_overflow_reports_and_truncates():
     rec10[:, 0], rec10[:, 1], rec10[:, 9] = u, v, z
     rec10[:, 2:5], rec10[:, 5] = conic, opac
     g = rec_to_gpu(rec10, r)
-    cfg = N.make_config(W, H, B, 64, 0)
-    _, vals_o = O.bin_lists(u, v, z, r, V, n, W, H, B, conic=conic, tau=O.tau32(opac))
+    cfg = N.make_config(W, H, B, 64, 0, rect_lists=True)
+    _, vals_o = O.bin_lists(u, v, z, r, V, n, W, H, B)
     cap = len(vals_o) // 3
     vals, ranges, _, ninst, st = gpu_bin(N, g, n, V, cfg, cap)
     assert st == N.CGS_ERR_CAPACITY
@@ -236,10 +328,10 @@ def stage_inputs(name, bg=(0.0, 0.0, 0.0)):
 
 
 def gpu_forward_from_rec(N, sc, rec, pre, tgt_rgb, tgt_d, batch_depth=64, bg=(0.0, 0.0, 0.0), order=True,
-                         cap=1 << 22):
+                         cap=1 << 22, rect_lists=False):
     torch = torch_cuda()
     V, n, H, W = sc.views, sc.n, sc.height, sc.width
-    cfg = cfg_for(N, sc, batch_depth, bg=bg)
+    cfg = cfg_for(N, sc, batch_depth, bg=bg, rect_lists=rect_lists)
     g = rec_to_gpu(rec, pre["radius"])
     vals, ranges, tord, ninst, st = gpu_bin(N, g, n, V, cfg, cap, order)
     assert st == 0
@@ -267,9 +359,11 @@ def test_render_fwd_matches_oracle(name, bd):
     N = native()
     sc, tgt_rgb, tgt_d, pre, rec, ranges, vals, fw = stage_inputs(name)
     out = gpu_forward_from_rec(N, sc, rec, pre, tgt_rgb, tgt_d, bd, cap=len(vals) + 16)
-    # identical float32 inputs -> identical tile lists
-    assert np.array_equal(out["ranges"].cpu().numpy().view(np.uint32).reshape(-1, 2), ranges)
-    assert np.array_equal(out["vals"].cpu().numpy().view(np.uint32)[: len(vals)], vals)
+    # the oracle blends the rect lists, the GPU its culled lists of the same float32 records
+    grg, gvals = out["ranges"].cpu().numpy().view(np.uint32).reshape(-1, 2), None
+    gvals = out["vals"].cpu().numpy().view(np.uint32)[: int(grg[-1, 1])]
+    tot, kept, dropped = check_culled_lists(out["rec"].cpu().numpy().reshape(-1, 12), ranges, vals, grg, gvals,
+                                            sc.width, sc.height, sc.tile)
     ok = fw["near"] == 0
     frac = 1.0 - ok.mean()
     assert frac < 2e-4
@@ -280,12 +374,36 @@ def test_render_fwd_matches_oracle(name, bd):
     e_T = np.abs(out["T"].cpu().numpy() - fw["T"])[ok].max()
     dscale = max(1.0, np.abs(fw["depth"]).max())
     e_d = (np.abs(out["depth"].cpu().numpy() - fw["depth"])[ok]).max() / dscale
-    last_ok = np.mean(out["last"].cpu().numpy().view(np.uint32)[ok] == fw["last"][ok])
+    # the last blended splat of every pixel is the same splat on both sides
+    ls_g = last_slots(out["last"].cpu().numpy(), grg, gvals, sc.width, sc.height, sc.tile)
+    ls_o = last_slots(fw["last"], ranges, vals, sc.width, sc.height, sc.tile)
     assert e_img < PIX_TOL and e_T < PIX_TOL and e_d < PIX_TOL
-    assert last_ok == 1.0
+    assert np.array_equal(ls_g[ok], ls_o[ok])
     np.testing.assert_allclose(out["loss"].cpu().numpy(), fw["loss_view"], rtol=2e-5)
     assert np.array_equal(out["dcount"].cpu().numpy(), fw["depth_count"])
-    print(f"[fwd {name}] excluded {frac:.2e} max|dimg| {e_img:.2e} |dT| {e_T:.2e} |ddepth|/scale {e_d:.2e}")
+    print(f"[fwd {name}] lists: rect {tot} kept {kept} dropped {dropped}; excluded {frac:.2e} "
+          f"max|dimg| {e_img:.2e} |dT| {e_T:.2e} |ddepth|/scale {e_d:.2e}")
+
+
+@pytest.mark.parametrize("name", ["cfg1", "room_sh3_20k", "room_t32"])
+def test_render_fwd_rect_lists_equal_culled_lists(name):
+    """The same records blended from the rect lists and from the culled lists: images,
+    depth, transmittance and loss bit-identical, and each pixel's last blended splat the same."""
+    torch = torch_cuda()
+    N = native()
+    sc, tgt_rgb, tgt_d, pre, rec, ranges, vals, fw = stage_inputs(name)
+    outs = {}
+    for rect in (False, True):
+        o = gpu_forward_from_rec(N, sc, rec, pre, tgt_rgb, tgt_d, 128, cap=len(vals) + 16, rect_lists=rect)
+        rg = o["ranges"].cpu().numpy().view(np.uint32).reshape(-1, 2)
+        vv = o["vals"].cpu().numpy().view(np.uint32)[: int(rg[-1, 1])]
+        if rect:
+            assert np.array_equal(rg, ranges) and np.array_equal(vv, vals)
+        outs[rect] = (o, last_slots(o["last"].cpu().numpy(), rg, vv, sc.width, sc.height, sc.tile))
+    (a, la), (b, lb) = outs[False], outs[True]
+    for k in ("img", "depth", "T", "loss", "dcount"):
+        assert torch.equal(a[k], b[k]), k
+    assert np.array_equal(la, lb)
 
 
 def test_render_fwd_work_counts_on_request():
@@ -347,11 +465,10 @@ def test_raster_bwd_matches_oracle(name, bd):
     g = sg_from_gpu(sg)
     ref = O.render_bwd(rec, ranges, vals, V, n, sc.width, sc.height, sc.tile, sc.cams, fw["img"], fw["depth"],
                        tgt_rgb, tgt_d, fw["depth_count"])
-    fields = ["u", "v", "A", "B", "C", "o", "r", "g", "b", "z"]
-    errs = {f: rel_l2(g[:, k], ref[:, k]) for k, f in enumerate(fields)}
-    print(f"[bwd {name}] " + " ".join(f"{f}:{e:.1e}" for f, e in errs.items()))
-    for f, e in errs.items():
-        assert e < GRAD_REL_TOL, (f, e)
+    near = slots_in_flagged_tiles(fw["near"], ranges, vals, sc.width, sc.height, sc.tile, V * n)
+    print(f"[bwd {name}] slots in tiles with a flagged pixel: {near.sum()} of {(np.abs(ref).sum(1) > 0).sum()}")
+    for k, f in enumerate(FIELDS):
+        grad_check(g[:, k], ref[:, k], near, f)
 
 
 @pytest.mark.parametrize("name", ["cfg1", "cfg3", "tiny_sh3_3views", "room_sh3_20k"])
@@ -377,9 +494,9 @@ def test_preprocess_bwd_matches_oracle(name):
     # projections may decide differently
     ref = O.preprocess_bwd(sc.params, n, sc.sh_degree, sc.cams, sc.width, sc.height, sc.tile, sg32)
     gg = grads.cpu().numpy().astype(np.float64)
-    for gname, sl in group_slices(n, sc.sh_degree).items():
-        e = rel_l2(gg[sl], ref[sl])
-        assert e < 1e-4 or (pre["fragile"].any() and e < GRAD_REL_TOL), (gname, e)
+    fragile_g = gaussians_of_slots(pre["fragile"] > 0, n)
+    param_grad_check(gg, ref, n, sc.sh_degree, fragile_g, f"pre bwd {name}",
+                     l2=GRAD_REL_TOL if fragile_g.any() else 1e-4)
     a_o, d_o, m_o = O.densify_stats(sg32, pre["radius"], V, n, sc.width, sc.height)
     np.testing.assert_allclose(acc.cpu().numpy(), a_o, rtol=1e-5, atol=1e-9)
     assert np.array_equal(den.cpu().numpy(), d_o)
@@ -418,11 +535,18 @@ def test_window_iteration_matches_oracle(name):
     assert 1 - ok.mean() < 1e-3
     np.testing.assert_allclose(win.loss_view.cpu().numpy(), it["fwd"]["loss_view"], rtol=1e-4)
     gg = win.grads.cpu().numpy().astype(np.float64)
-    errs = {k: rel_l2(gg[sl], it["grads"][sl]) for k, sl in group_slices(sc.n, sc.sh_degree).items()}
-    print(f"[iter {name}] excluded px {1 - ok.mean():.2e} flipped {(err > PIX_TOL).mean():.2e} max|dimg| {e_img:.2e} " +
-          " ".join(f"{k}:{e:.1e}" for k, e in errs.items()))
-    for k, e in errs.items():
-        assert e < GRAD_REL_TOL, (k, e)
+    print(f"[iter {name}] excluded px {1 - ok.mean():.2e} flipped {(err > PIX_TOL).mean():.2e} max|dimg| {e_img:.2e}")
+    param_grad_check(gg, it["grads"], sc.n, sc.sh_degree, iteration_near_gaussians(sc, it), f"iter {name}")
+
+
+def iteration_near_gaussians(sc, it, reach_px=0):
+    """Gaussians the oracle's iteration marks as possibly deciding differently in float32: a
+    slot listed in a tile with a flagged pixel (or one within reach_px of it), or a slot
+    whose projection is fragile."""
+    m = sc.views * sc.n
+    near = slots_in_flagged_tiles(it["fwd"]["near"], it["ranges"], it["vals"], sc.width, sc.height, sc.tile, m,
+                                  reach_px)
+    return gaussians_of_slots(near | (it["pre"]["fragile"] > 0), sc.n)
 
 
 def test_batched_equals_per_view():
@@ -443,8 +567,7 @@ def test_batched_equals_per_view():
     a, b = wins
     assert torch.equal(a.img, b.img) and torch.equal(a.last, b.last)
     torch.testing.assert_close(a.loss_view, b.loss_view, rtol=1e-6, atol=0)
-    for k, sl in group_slices(sc.n, 3).items():
-        assert rel_l2(a.grads[sl].cpu().numpy(), b.grads[sl].cpu().numpy()) < 1e-5, k
+    param_grad_check(a.grads.cpu().numpy(), b.grads.cpu().numpy(), sc.n, 3, None, "batched vs per-view", l2=1e-5)
     assert torch.equal(a.denom, b.denom) and torch.equal(a.max_r2d, b.max_r2d)
     torch.testing.assert_close(a.accum, b.accum, rtol=1e-5, atol=1e-12)
 
@@ -567,7 +690,7 @@ def test_single_gaussian_single_pixel_image():
     torch.cuda.synchronize()
     it = O.iteration(sc.params, 1, 0, sc.cams, 1, 1, 8, tgt.astype(np.float64), np.ones((1, 1, 1)))
     assert abs(win.img.cpu().numpy() - it["fwd"]["img"]).max() < PIX_TOL
-    assert rel_l2(win.grads.cpu().numpy(), it["grads"]) < GRAD_REL_TOL
+    param_grad_check(win.grads.cpu().numpy(), it["grads"], 1, 0, None, "1x1")
 
 
 def test_bad_arguments_raise_before_launch():
@@ -599,8 +722,8 @@ def test_autograd_functions_match_fused_backward():
     p = params.clone().requires_grad_(True)
     loss = RasterizeWindow.apply(p, win).sum()
     loss.backward()
-    for k, sl in group_slices(sc.n, 3).items():
-        assert rel_l2(p.grad[sl].cpu().numpy(), it["grads"][sl]) < GRAD_REL_TOL, k
+    near_g = iteration_near_gaussians(sc, it)
+    param_grad_check(p.grad.cpu().numpy(), it["grads"], sc.n, 3, near_g, "autograd loss")
     # image-level autograd with the same L1 loss written in torch
     p2 = params.clone().requires_grad_(True)
     img, dep = RenderWindow.apply(p2, win)
@@ -611,8 +734,7 @@ def test_autograd_functions_match_fused_backward():
     l2 = (img - tr).abs().sum(dim=(1, 2, 3)) / (3 * HW)
     ld = ((dep - td).abs() * valid).sum(dim=(1, 2)) / valid.sum(dim=(1, 2))
     (l2 + 0.1 * ld).sum().backward()
-    for k, sl in group_slices(sc.n, 3).items():
-        assert rel_l2(p2.grad[sl].cpu().numpy(), it["grads"][sl]) < GRAD_REL_TOL, k
+    param_grad_check(p2.grad.cpu().numpy(), it["grads"], sc.n, 3, near_g, "autograd image")
 
 
 # ------------------------------------------------- splat-wise backward (Fig. 4a)
@@ -638,7 +760,8 @@ def test_splat_backward_matches_oracle(name, bd, tile):
     gv, gr, go, ninst, st = gpu_bin(N, g, n, V, cfg, cap)
     assert st == 0
     Ttot = N.cgs_tiles_per_view(cfg) * V
-    nb = int(sum((int(e) - int(s0) + 31) // 32 for s0, e in ranges))
+    grg = gr.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    nb = int(((grg[:, 1] - grg[:, 0] + 31) // 32).sum())
     ckpt = torch.zeros(N.cgs_ckpt_bytes(nb, cfg) // 4, device="cuda")
     bstart = torch.zeros(Ttot + 1, dtype=torch.int32, device="cuda")
     out = {k: torch.zeros(V, 3, H, W, device="cuda") if k == "img" else torch.zeros(V, H, W, device="cuda")
@@ -661,11 +784,9 @@ def test_splat_backward_matches_oracle(name, bd, tile):
     ok = fw["near"] == 0
     assert np.abs(out["img"].cpu().numpy() - fw["img"]).max(1)[ok].max() < PIX_TOL
     gg = sg_from_gpu(sg)
-    fields = ["u", "v", "A", "B", "C", "o", "r", "g", "b", "z"]
-    errs = {f: rel_l2(gg[:, k], ref[:, k]) for k, f in enumerate(fields)}
-    print(f"[splat bwd {name}] " + " ".join(f"{f}:{e:.1e}" for f, e in errs.items()))
-    for f, e in errs.items():
-        assert e < GRAD_REL_TOL, (f, e)
+    near = slots_in_flagged_tiles(fw["near"], ranges, vals, W, H, tile, V * n)
+    for k, f in enumerate(FIELDS):
+        grad_check(gg[:, k], ref[:, k], near, f"splat bwd {name} {f}")
 
 
 def test_splat_window_iteration_equals_pixel_window_iteration():
@@ -687,8 +808,7 @@ def test_splat_window_iteration_equals_pixel_window_iteration():
         wins[kind] = win
     a, b = wins["pixel"], wins["splat"]
     assert torch.equal(a.img, b.img) and torch.equal(a.last, b.last)
-    for k, sl in group_slices(sc.n, 3).items():
-        assert rel_l2(b.grads[sl].cpu().numpy(), a.grads[sl].cpu().numpy()) < 1e-4, k
+    param_grad_check(b.grads.cpu().numpy(), a.grads.cpu().numpy(), sc.n, 3, None, "splat vs pixel", l2=1e-4)
     assert torch.equal(a.denom, b.denom)
 
 
@@ -852,10 +972,9 @@ def test_window_ssim_iteration_matches_oracle(name):
                      tol=1e-4, lambda_ssim=0.2)
     np.testing.assert_allclose(win.loss_view.cpu().numpy(), it["loss_view"], rtol=1e-4)
     gg = win.grads.cpu().numpy().astype(np.float64)
-    errs = {k: rel_l2(gg[sl], it["grads"][sl]) for k, sl in group_slices(sc.n, sc.sh_degree).items()}
-    print(f"[ssim iter {name}] " + " ".join(f"{k}:{e:.1e}" for k, e in errs.items()))
-    for k, e in errs.items():
-        assert e < GRAD_REL_TOL, (k, e)
+    # the SSIM gradient of a pixel reads the images 10 pixels around it
+    param_grad_check(gg, it["grads"], sc.n, sc.sh_degree, iteration_near_gaussians(sc, it, reach_px=10),
+                     f"ssim iter {name}")
 
 
 def test_ssim_batched_per_view_and_splat_agree():
@@ -878,8 +997,7 @@ def test_ssim_batched_per_view_and_splat_agree():
     for kind in ("per_view", "splat"):
         b = wins[kind]
         torch.testing.assert_close(a.loss_view, b.loss_view, rtol=1e-6, atol=0)
-        for k, sl in group_slices(sc.n, 3).items():
-            assert rel_l2(b.grads[sl].cpu().numpy(), a.grads[sl].cpu().numpy()) < 1e-4, (kind, k)
+        param_grad_check(b.grads.cpu().numpy(), a.grads.cpu().numpy(), sc.n, 3, None, f"ssim {kind}", l2=1e-4)
 
 
 # ----------------------------------------------------- geometric densification
@@ -1028,6 +1146,8 @@ def test_staged_window_inputs_equal_direct_copy():
     b.stage_window(h_cams, h_rgb, h_d)
     b.forward()                                              # renders the stale inputs meanwhile
     b.commit_window()
+    with pytest.raises(RuntimeError):
+        b.commit_window()                                    # nothing new staged
     b.replay()
     a.step()
     torch.cuda.synchronize()

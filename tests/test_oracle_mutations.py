@@ -46,10 +46,10 @@ MUTATIONS = [
      [TG.test_densify_stats_hand_example]),
     ("if (acc < 0.0) { acc = 0.0;", "if (0) { acc = 0.0;",
      [TP.test_sh_degree0_colour_is_view_independent_and_clamped]),
-    ("float bc = B / C, ba = B / A, B2 = 2.0f * B;", "float bc = B / C, ba = B / A, B2 = B;",
-     [lambda: TR.test_bin_lists_with_reach_test_brute_force(0)]),
-    ("float ddy = fminf(fmaxf(-(bc * ddx), v - by1), v - by0);", "float ddy = fminf(fmaxf(bc * ddx, v - by1), v - by0);",
-     [lambda: TR.test_bin_lists_with_reach_test_brute_force(1)]),
+    ("rect[2] = clampi(floordiv(fv - r, B), 0, Ty);", "rect[2] = clampi(floordiv(fv - r + 1, B), 0, Ty);",
+     [lambda: TR.test_bin_lists_brute_force(2), lambda: TR.test_tiled_render_matches_brute_force(3)]),
+    ("if (a->z != b->z) return a->z < b->z ? -1 : 1;", "if (a->z != b->z) return a->z > b->z ? -1 : 1;",
+     [lambda: TR.test_tiled_render_matches_brute_force(3)]),
 ]
 
 

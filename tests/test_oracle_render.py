@@ -122,22 +122,16 @@ def brute_render(rec, radius, rect, n, W, H, B):
     return img, Tf
 
 
-@pytest.mark.parametrize("reach", [False, True])
-def test_tiled_render_matches_brute_force(reach):
-    # with or without the tile reach test, a tile's list holds every splat that blends
-    # at one of its pixels: the tiled render equals the render over all Gaussians
-    sc = make_tiny_scene(seed=3, n=30, sh_degree=1, W=24, H=16, views=1, tile=8)
+@pytest.mark.parametrize("seed", [3, 8])
+def test_tiled_render_matches_brute_force(seed):
+    # a tile's list holds every splat whose rect covers the tile, so the tiled render equals
+    # the render over all Gaussians
+    sc = make_tiny_scene(seed=seed, n=30, sh_degree=1, W=24, H=16, views=1, tile=8)
     cams = sc.cams
     pre = O.preprocess(sc.params, sc.n, 1, cams, sc.width, sc.height, sc.tile)
     rec = pre["rec"]
-    if reach:
-        ranges, vals = O.bin_records(rec, pre["radius"], 1, sc.n, sc.width, sc.height, sc.tile)
-        full, _ = O.bin_lists(rec[:, 0], rec[:, 1], rec[:, 9], pre["radius"], 1, sc.n,
-                              sc.width, sc.height, sc.tile)
-        assert ranges[-1, 1] < full[-1, 1]              # the test does drop instances here
-    else:
-        ranges, vals = O.bin_lists(rec[:, 0], rec[:, 1], rec[:, 9], pre["radius"], 1, sc.n,
-                                   sc.width, sc.height, sc.tile)
+    ranges, vals = O.bin_lists(rec[:, 0], rec[:, 1], rec[:, 9], pre["radius"], 1, sc.n,
+                               sc.width, sc.height, sc.tile)
     fw = O.render_fwd(rec, ranges, vals, 1, sc.width, sc.height, sc.tile, cams)
     img, Tf = brute_render(rec, pre["radius"], pre["rect"], sc.n, sc.width, sc.height, sc.tile)
     assert (pre["radius"] > 0).sum() > 10
@@ -206,93 +200,3 @@ def test_render_pixels_matches_full_render():
     np.testing.assert_array_equal(px["img"], fw["img"][0][:, pix[:, 2], pix[:, 1]].T)
     np.testing.assert_array_equal(px["T"], fw["T"][0][pix[:, 2], pix[:, 1]])
     np.testing.assert_array_equal(px["last"], fw["last"][0][pix[:, 2], pix[:, 1]])
-
-
-def reach_touches_np(u, v, A, B, C, tau, bx0, bx1, by0, by1):
-    """The tile reach test written out in numpy float32 arrays, one IEEE rounding per
-    operation, in the order the oracle and the kernels take them."""
-    f = np.float32
-    u, v, A, B, C, tau = (np.asarray(x, np.float32) for x in (u, v, A, B, C, tau))
-    bx0, bx1, by0, by1 = (np.asarray(x, np.float32) for x in (bx0, bx1, by0, by1))
-    live = tau <= f(1e-4)
-    det = A * C - B * B
-    with np.errstate(divide="ignore", invalid="ignore"):
-        t2 = (f(-2.0) * tau) * f(1.001) + f(1e-3)
-        ex = np.sqrt(t2 * C / det) + f(1e-2)
-        ey = np.sqrt(t2 * A / det) + f(1e-2)
-        dx = np.abs(u - np.minimum(np.maximum(u, bx0), bx1))
-        dy = np.abs(v - np.minimum(np.maximum(v, by0), by1))
-        box = (dx <= ex) & (dy <= ey)
-        inside = (dx == 0) & (dy == 0)
-        bc, ba, B2 = B / C, B / A, f(2.0) * B
-        qmin = np.full(u.shape, np.inf, np.float32)
-        for X in (bx0, bx1):
-            ddx = u - X
-            ddy = np.minimum(np.maximum(-(bc * ddx), v - by1), v - by0)
-            qmin = np.minimum(qmin, ((A * ddx) * ddx + (B2 * ddx) * ddy) + (C * ddy) * ddy)
-        for Y in (by0, by1):
-            ddy = v - Y
-            ddx = np.minimum(np.maximum(-(ba * ddy), u - bx1), u - bx0)
-            qmin = np.minimum(qmin, ((A * ddx) * ddx + (B2 * ddx) * ddy) + (C * ddy) * ddy)
-    return live & (~(det > 0) | (box & (inside | (qmin <= t2))))
-
-
-@pytest.mark.parametrize("seed", range(3))
-def test_bin_lists_with_reach_test_brute_force(seed):
-    # the rect's tiles, kept by the reach test computed independently in numpy float32
-    from synth import make_conics
-    V, n, W, H, B = 2, 300, 96, 64, 16
-    u, v, r, z = make_records(seed, V, n, W, H, max_radius=24)
-    conic, opac = make_conics(seed + 7, r)
-    tau = O.tau32(opac)
-    ranges, vals = O.bin_lists(u, v, z, r, V, n, W, H, B, conic=conic, tau=tau)
-    Tx, Ty = (W + B - 1) // B, (H + B - 1) // B
-    expect = {}
-    dropped = 0
-    for s in range(V * n):
-        if r[s] <= 0:
-            continue
-        uu, vv, rr = float(u[s]), float(v[s]), int(r[s])
-        x0 = min(max(math.floor((uu - rr) / B), 0), Tx)
-        x1 = min(max(math.floor((uu + rr + B - 1) / B), 0), Tx)
-        y0 = min(max(math.floor((vv - rr) / B), 0), Ty)
-        y1 = min(max(math.floor((vv + rr + B - 1) / B), 0), Ty)
-        for ty in range(y0, y1):
-            for tx in range(x0, x1):
-                bx1, by1 = min(tx * B + B, W) - 1, min(ty * B + B, H) - 1
-                if not reach_touches_np(u[s], v[s], conic[s, 0], conic[s, 1], conic[s, 2], tau[s],
-                                        tx * B, bx1, ty * B, by1):
-                    dropped += 1
-                    continue
-                expect.setdefault((s // n) * Tx * Ty + ty * Tx + tx, []).append(s)
-    assert dropped > 0.1 * len(vals)
-    pos = 0
-    for t in range(V * Tx * Ty):
-        st, en = ranges[t]
-        assert st == pos
-        assert list(vals[st:en]) == sorted(expect.get(t, []), key=lambda s: (float(z[s]), s))
-        pos = en
-    assert pos == len(vals)
-
-
-def test_reach_test_is_conservative_and_drops_a_missed_tile():
-    # a thin ellipse along the diagonal from (20, 20): its bounding box reaches the box
-    # [24, 39] x [0, 15] (tile (1, 0) of 16x16) but the ellipse does not; every pixel
-    # whose alpha (in double) is at least 1/255 lies in a box the test keeps
-    lmax, lmin, th = 40.0, 0.6, np.pi / 4
-    c, s = np.cos(th), np.sin(th)
-    sxx, syy, sxy = c * c * lmax + s * s * lmin, s * s * lmax + c * c * lmin, c * s * (lmax - lmin)
-    det = sxx * syy - sxy * sxy
-    A, Bc, C = syy / det, -sxy / det, sxx / det
-    o = 0.8
-    tau = O.tau32([o])[0]
-    u, v = 20.0, 20.0
-    keep = lambda bx0, bx1, by0, by1: bool(reach_touches_np(u, v, A, Bc, C, tau, bx0, bx1, by0, by1))  # noqa: E731
-    assert keep(0, 15, 0, 15) and keep(16, 31, 16, 31)
-    assert not keep(24, 39, 0, 15)
-    ys, xs = np.mgrid[0:64, 0:64]
-    dx, dy = u - xs, v - ys
-    alpha = o * np.exp(-0.5 * (A * dx * dx + 2 * Bc * dx * dy + C * dy * dy))
-    for y, x in zip(*np.nonzero(alpha >= 1.0 / 255.0)):
-        bx0, by0 = (x // 8) * 8, (y // 8) * 8
-        assert keep(bx0, bx0 + 7, by0, by0 + 7), (x, y)
