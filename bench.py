@@ -1,19 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the CaRtGS mapping iteration on GB300.
 
-Workload: a 16-view 1200x680 keyframe window of a 300k-Gaussian SH-degree-3 room
-scene (opacity logits N(-1, 1.5)), synthetic and seeded.  One step = one batched
-window iteration: preprocess, bin sort, forward blend + L1 RGB/depth loss, backward,
-densification statistics, fused Adam -- replayed from a captured CUDA graph with
-every input resident in HBM (the working set is several GB, larger than L2).
+Default workload: a 16-view 1200x680 keyframe window of a 300k-Gaussian SH-degree-3
+room scene (opacity logits N(-1, 1.5)), synthetic and seeded; --config 1-4 picks the
+other workload shapes (2k-Gaussian 160x120 view, 100k-Gaussian 1200x680 view, 5k-Gaussian
+320x240 view, 8-view 640x480 window of 200k Gaussians).  One step = one batched window
+iteration: preprocess, bin sort, forward blend + L1 RGB/depth loss, backward,
+densification statistics, fused Adam -- replayed from a captured CUDA graph with every
+input resident in HBM.
 
-Prints ONE JSON line (rank 0).  Besides the timed value it reports the same
-iteration in the plain per-view form, the end-to-end rate through the public API
-with the window's inputs copied from pinned host memory every step, a per-stage
-breakdown, the roofline of the dominant kernel, and the FP64 oracle timed on the
-host cores as a CPU baseline.
+Prints ONE JSON line (rank 0).  Besides the timed value it reports the same iteration in
+the plain per-view form and in the paper's sequential loop (Adam after every view), the
+end-to-end rate through the public API with the window's inputs copied from pinned host
+memory every step, per-stage times with each stage's roofline fraction, the whole
+iteration's fraction of the HBM roofline, the roofline of the dominant kernel, and the
+FP64 oracle timed on the host cores as a CPU baseline.
 
-  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference] [--config 1-5]
 """
 from __future__ import annotations
 
@@ -34,15 +37,20 @@ if str(ROOT) not in sys.path:
 
 METRIC = "mapping window iterations/s (fwd+bwd+Adam)"
 UNIT = "window_iter/s"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+TRAFFIC_FILE = ROOT / "ncu_traffic.json"
 
-# Work model of the raster kernels, in FP32 instructions per (splat, pixel) pair, counted
-# from the kernel source: evaluating a pair (offsets, exponent, exp, alpha, tests) and,
-# for a blended pair, the extra blend / gradient work.
+# Work model of the raster kernels: formula operations per (splat, pixel) pair, as the
+# blend and its derivative are written out (Eq. 1, Eqs. 2-4): evaluating a pair (offsets,
+# exponent, exp, alpha, the two threshold tests) and, for a blended pair, the extra blend
+# (forward) or gradient (backward) work.  The kernels execute fewer instructions than this
+# (shared column terms, one dot product for the colour behind), so the achieved rate is
+# formula operations per second.
 FWD_OPS_EVAL, FWD_OPS_BLEND = 13, 11
 BWD_OPS_EVAL, BWD_OPS_BLEND = 13, 55
+# Replays timed for each alternative form of the iteration (per-view, paper loop, splat-wise
+# backward, SSIM loss, end to end): at least this many, or --steps if larger.
+MIN_FORM_STEPS = 20
 
 
 def parse():
@@ -129,22 +137,40 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- oracle side
 
-def oracle_view_iteration(sc, v, row0=0, rows=None, lambda_d=0.1):
-    """One view-iteration of the FP64 oracle on rows [row0, row0+rows) of view v (a crop is
-    the same sub-problem: cy shifted, tile-aligned rows).  Targets are the oracle's render
-    of the perturbed copy.  Returns seconds spent on the timed part (fwd+bwd, not targets)."""
+BAND_TILE_ROWS = 5      # a CPU sample step covers this many tile rows of every view
+
+
+def oracle_targets_band(sc, row0, rows):
+    """The oracle's render of the perturbed copy on rows [row0, row0 + rows) of every view
+    (a crop is the same sub-problem with cy shifted): the targets of a sample step."""
     from oracle import oracle as O
-    H = sc.height if rows is None else rows
-    cam = sc.cams[v:v + 1].astype(np.float64).copy()
-    cam[0, 15] -= row0
-    pre_t = O.preprocess(sc.params_target, sc.n, sc.sh_degree, cam, sc.width, H, sc.tile)
-    r = pre_t["rec"]
-    rg, vl = O.bin_lists(r[:, 0], r[:, 1], r[:, 9], pre_t["radius"], 1, sc.n, sc.width, H, sc.tile)
-    tg = O.render_fwd(r, rg, vl, 1, sc.width, H, sc.tile, cam)
+    cams = sc.cams.astype(np.float64).copy()
+    cams[:, 15] -= row0
+    pre = O.preprocess(sc.params_target, sc.n, sc.sh_degree, cams, sc.width, rows, sc.tile)
+    rg, vl = O.bin_records(pre["rec"], pre["radius"], sc.views, sc.n, sc.width, rows, sc.tile)
+    tg = O.render_fwd(pre["rec"], rg, vl, sc.views, sc.width, rows, sc.tile, cams)
+    return cams, tg["img"], tg["depth"]
+
+
+def oracle_band_step(sc, cams, tgt_rgb, tgt_d, rows, views=None, lambda_d=0.1):
+    """One sample step of the FP64 oracle, as it stands: the iteration's steps (projection,
+    rect lists, blend + L1 loss, hand-derived backward, chain rule to the parameters) on a
+    band of `rows` rows of every view (or of `views`).  Returns (seconds of the projection,
+    seconds of the whole step)."""
+    from oracle import oracle as O
+    if views is not None:
+        cams, tgt_rgb, tgt_d = cams[views], tgt_rgb[views], tgt_d[views]
+    V = cams.shape[0]
     t0 = time.perf_counter()
-    O.iteration(sc.params, sc.n, sc.sh_degree, cam, sc.width, H, sc.tile, tg["img"], tg["depth"],
-                lambda_d=lambda_d)
-    return time.perf_counter() - t0
+    pre = O.preprocess(sc.params, sc.n, sc.sh_degree, cams, sc.width, rows, sc.tile)
+    t1 = time.perf_counter()
+    rec = pre["rec"]
+    rg, vl = O.bin_records(rec, pre["radius"], V, sc.n, sc.width, rows, sc.tile)
+    fw = O.render_fwd(rec, rg, vl, V, sc.width, rows, sc.tile, cams, (0.0, 0.0, 0.0), tgt_rgb, tgt_d, lambda_d)
+    sg = O.render_bwd(rec, rg, vl, V, sc.n, sc.width, rows, sc.tile, cams, fw["img"], fw["depth"], tgt_rgb, tgt_d,
+                      fw["depth_count"], (0.0, 0.0, 0.0), lambda_d)
+    O.preprocess_bwd(sc.params, sc.n, sc.sh_degree, cams, sc.width, rows, sc.tile, sg)
+    return t1 - t0, time.perf_counter() - t0
 
 
 def oracle_adam_seconds(P):
@@ -158,62 +184,123 @@ def oracle_adam_seconds(P):
     return time.perf_counter() - t0
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def band_rows(sc):
+    return min(sc.height, BAND_TILE_ROWS * sc.tile)
+
+
+def window_seconds_from_band(sc, t_pre, t_step, rows, t_adam):
+    """A window iteration's oracle time from a band sample: the projection of every Gaussian
+    is paid once per window (measured on the band), the rest scales with the image rows, and
+    Adam runs once on all parameters."""
+    return t_pre + (sc.height / rows) * (t_step - t_pre) + t_adam
+
+
 def cpu_baseline(sc):
-    """The oracle, as it stands, on a bounded sample: one full view-iteration of view 0
-    (all Gaussians, full resolution) plus Adam on the whole parameter vector; scaled to
-    window iterations/s (V view-iterations + one Adam per window)."""
-    t_view = oracle_view_iteration(sc, 0)
+    """The oracle, as it stands, on bounded samples of the workload: a band of tile rows of
+    every view on all host cores, and the same band of one view on one core; each scaled to
+    a window iteration (window_seconds_from_band) with Adam on all parameters."""
+    from oracle import oracle as O
+    cores = host_cores()
+    rows = band_rows(sc)
+    cams, tr, td = oracle_targets_band(sc, 0, rows)
     t_adam = oracle_adam_seconds(sc.params.size)
-    t_window = sc.views * t_view + t_adam
-    return {"value": 1.0 / t_window, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 of {sc.views} views at full resolution ({t_view:.2f} s) + Adam on all "
-                      f"{sc.params.size} parameters ({t_adam:.2f} s), scaled to a {sc.views}-view window"}
+    O.set_threads(cores)
+    t_pre, t_step = oracle_band_step(sc, cams, tr, td, rows)
+    t_win = window_seconds_from_band(sc, t_pre, t_step, rows, t_adam)
+    O.set_threads(1)
+    t_pre1, t_step1 = oracle_band_step(sc, cams, tr, td, rows, views=[0])
+    t_win1 = sc.views * (t_pre1 + (sc.height / rows) * (t_step1 - t_pre1)) + t_adam
+    O.set_threads(cores)
+    return {"value": 1.0 / t_win, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"rows 0-{rows - 1} of all {sc.views} views, all {sc.n} Gaussians, fwd+bwd on {cores} "
+                      f"threads ({t_step:.2f} s, projection {t_pre:.2f} s), scaled to {sc.height} rows; "
+                      f"+ Adam on all {sc.params.size} parameters ({t_adam:.2f} s)",
+            "value_1core": 1.0 / t_win1,
+            "sample_1core": f"the same band of view 0 on 1 thread ({t_step1:.2f} s), scaled to {sc.height} rows "
+                            f"and {sc.views} views, + Adam"}
 
 
 def run_reference(args):
-    """--impl reference: the FP64 oracle timed on the host cores on the same workload;
-    each step is a bounded sample (a quarter-height, tile-aligned band of one view)."""
+    """--impl reference: the FP64 oracle, as it stands, timed on all host cores on the same
+    workload; each step is a bounded sample (a band of tile rows of every view, the bands
+    taken in turn), and the value is the window iterations/s those samples imply."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from oracle import oracle as O
     from synth import make_scene
     sc = make_scene(args.config)
-    band = (sc.height // 4 // sc.tile) * sc.tile
-    bands = -(-sc.height // band)
+    cores = host_cores()
+    O.set_threads(cores)
+    rows = band_rows(sc)
+    nb = max(1, sc.height // rows)                  # whole bands only
+    targets = {}
     t_adam = oracle_adam_seconds(sc.params.size)
-    for w in range(args.warmup):
-        oracle_view_iteration(sc, w % sc.views, (w % bands) * band, min(band, sc.height - (w % bands) * band))
     ts = []
-    for k in range(args.steps):
-        b = k % bands
-        rows = min(band, sc.height - b * band)
-        ts.append(oracle_view_iteration(sc, k % sc.views, b * band, rows) * (sc.height / rows))
-    t_window = sc.views * float(np.mean(ts)) + t_adam
+    t_run0 = time.perf_counter()
+    for k in range(args.warmup + args.steps):
+        b = k % nb
+        if b not in targets:
+            targets[b] = oracle_targets_band(sc, b * rows, rows)
+        cams, tr, td = targets[b]
+        t_pre, t_step = oracle_band_step(sc, cams, tr, td, rows)
+        if k >= args.warmup:
+            ts.append((t_pre, t_step))
+    wall = time.perf_counter() - t_run0
+    t_pre = float(np.mean([a for a, _ in ts]))
+    t_step = float(np.mean([b for _, b in ts]))
+    t_window = window_seconds_from_band(sc, t_pre, t_step, rows, t_adam)
     value = 1.0 / t_window
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_window,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded room scene, no dataset)",
-        "config": workload_config(sc),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step: a {band}-row band of one view at full width, all "
-                                   f"{sc.n} Gaussians, fwd+bwd; scaled by {sc.height}/{band} rows and "
-                                   f"{sc.views} views, plus Adam on all parameters ({t_adam:.2f} s)"},
+        "data": "synthetic (seeded scene, no dataset)",
+        "config": workload_config(sc, {"tile": sc.tile}),
+        "ms_per_window": 1e3 * t_window, "wall_s": round(wall, 2),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: a {rows}-row band of all {sc.views} views (bands of rows taken "
+                                   f"in turn), all {sc.n} Gaussians, fwd+bwd on {cores} threads "
+                                   f"({1e3 * t_step:.0f} ms, projection {1e3 * t_pre:.0f} ms); window time = "
+                                   f"projection + {sc.height}/{rows} x the rest + Adam on all parameters "
+                                   f"({t_adam:.2f} s)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+WORKLOAD_TEXT = {
+    1: "synthetic box scene",
+    2: "synthetic room, Replica-like shape",
+    3: "synthetic box scene",
+    4: "synthetic room, TUM-like path with uneven visibility",
+    5: "synthetic room, opacity logits N(-1,1.5)",
+}
+
+
 def workload_config(sc, extra=None):
+    kind = next((t for c, t in WORKLOAD_TEXT.items() if sc.name == _config_name(c)), "synthetic scene")
     cfg = {"workload": f"{sc.views}-view {sc.width}x{sc.height} window, {sc.n} Gaussians, SH degree "
-                       f"{sc.sh_degree} (synthetic room, opacity logits N(-1,1.5))",
+                       f"{sc.sh_degree} ({kind})",
            "views": sc.views, "width": sc.width, "height": sc.height, "gaussians": sc.n,
            "sh_degree": sc.sh_degree, "parallelism": "replicas",
-           "l2": "working set (params, Adam state, records, images, targets) > 129 MB L2; no flush"}
+           "l2": "working set (params, Adam state, records, images, targets) > 129 MB L2; no flush"
+           if sc.n * sc.views >= 100_000 else "small case: no L2 flush between steps"}
     if extra:
         cfg.update(extra)
     return cfg
+
+
+def _config_name(c):
+    from synth.scenes import CONFIG_NAMES
+    return CONFIG_NAMES[c]
 
 
 # ----------------------------------------------------------------------- ours
@@ -233,6 +320,33 @@ def job_throughput(world: int, steps_per_rank: int, seconds: float) -> float:
     """Whole-job window iterations/s: every rank runs its own window (replicas), so the job
     completes world x steps windows in the slowest rank's time."""
     return world * steps_per_rank / seconds
+
+
+def timed_graph(fn, k, warmup):
+    """ms per call of fn() captured in a CUDA graph: warm-up replays, then k replays bracketed
+    by CUDA events on the launching stream."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn()
+    torch.cuda.current_stream().wait_stream(s)
+    with torch.cuda.graph(g):
+        fn()
+    for _ in range(warmup):
+        g.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(k):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    del g
+    return e0.elapsed_time(e1) / k
 
 
 def main():
@@ -264,6 +378,8 @@ def main():
     V, n, W, H = sc.views, sc.n, sc.width, sc.height
     params_t = torch.from_numpy(sc.params).to(dev)
     cams = torch.from_numpy(np.ascontiguousarray(sc.cams)).to(dev)
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = int(props.multi_processor_count)
 
     # targets: the GPU render of the perturbed copy (set-up, untimed)
     tgt_win = MappingWindow(torch.from_numpy(sc.params_target).to(dev), n, sc.sh_degree, W, H, V,
@@ -278,8 +394,10 @@ def main():
     tuned = None
     if args.autotune:
         from paper_2410_00486_gb300.autotune import autotune
+        t0 = time.perf_counter()
         (tile, bd, bdb), res = autotune(params_t, n, sc.sh_degree, W, H, cams, tgt_rgb, tgt_d, log=log)
-        tuned = {"x".join(map(str, c)): round(ms, 3) for c, ms in res.items()}
+        tuned = {"choice": [tile, bd, bdb], "seconds": round(time.perf_counter() - t0, 2),
+                 "candidates_ms": {"x".join(map(str, c)): round(ms, 3) for c, ms in res.items()}}
 
     win = MappingWindow(params_t.clone(), n, sc.sh_degree, W, H, V, tile=tile, batch_depth=bd,
                         batch_depth_bwd=bdb)
@@ -294,7 +412,7 @@ def main():
 
     uuid = None
     try:
-        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = "GPU-" + str(props.uuid)
     except Exception:
         pass
     if world > 1:
@@ -318,92 +436,86 @@ def main():
     # step counter (the launch list of the captured iteration shows these 13 kernels per step)
     launches_per_step = 13
     gpu_launches = args.steps * launches_per_step
+    clocks = clk.summary()
+    k_forms = max(MIN_FORM_STEPS, args.steps)
 
-    # --- plain per-view form (same math, one view at a time), also graph-captured
-    per_view = None
+    # --- plain per-view form (same math, one view at a time), and the paper's sequential loop
+    #     (Adam after every view), both graph-captured
+    per_view = paper_loop = None
     if not args.no_per_view:
         pv = MappingWindow(params_t.clone(), n, sc.sh_degree, W, H, V, tile=tile, batch_depth=bd,
                            batch_depth_bwd=bdb, capacity=win.capacity)
         pv.set_window(cams, tgt_rgb, tgt_d)
-        pv.step_per_view()
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        s = torch.cuda.Stream()
-        s.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(s):
-            pv.step_per_view()
-        torch.cuda.current_stream().wait_stream(s)
-        with torch.cuda.graph(g):
-            pv.step_per_view()
-        for _ in range(args.warmup):
-            g.replay()
-        k = max(3, args.steps // 4)
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(k):
-            g.replay()
-        e1.record()
-        torch.cuda.synchronize()
-        pv_ms = e0.elapsed_time(e1) / k
-        per_view = {"value": 1e3 / pv_ms, "unit": UNIT, "ms_per_step": pv_ms, "steps": k,
+        pv_ms = timed_graph(pv.step_per_view, k_forms, args.warmup)
+        per_view = {"value": 1e3 / pv_ms, "unit": UNIT, "ms_per_step": pv_ms, "steps": k_forms,
                     "speedup_batched_vs_per_view": (value / world) / (1e3 / pv_ms)}
-        del pv, g
+        pl_ms = timed_graph(lambda: pv.step_per_view(adam_every_view=True), k_forms, args.warmup)
+        paper_loop = {"value": V * 1e3 / pl_ms, "unit": "view_iter/s", "ms_per_view_iteration": pl_ms / V,
+                      "steps": k_forms, "what": f"{V} single-view iterations (fwd+bwd+Adam each), as the "
+                                               "paper's mapping loop takes one keyframe per iteration"}
+        if win.read_status()[0] != 0 or pv.read_status()[0] != 0:
+            raise SystemExit(f"device status (per-view forms): {pv.read_status()}")
+        del pv
         torch.cuda.empty_cache()
 
     # --- head to head: the paper's splat-wise backward (Fig. 4a) in the same iteration
     splat = None
     if not args.no_splat and tile in (8, 16):
         splat = splat_head_to_head(MappingWindow, params_t, sc, tile, bd, cams, tgt_rgb, tgt_d, win.capacity,
-                                   max(3, args.steps // 4), args.warmup, value / world)
+                                   k_forms, args.warmup, value / world)
 
     # --- the same iteration with the SSIM term of Eq. 9 in the loss
     ssim = None
     if not args.no_ssim:
         ssim = ssim_variant(MappingWindow, params_t, sc, tile, (bd, bdb), cams, tgt_rgb, tgt_d, win.capacity,
-                            max(3, args.steps // 4), args.warmup, args.lambda_ssim)
+                            k_forms, args.warmup, args.lambda_ssim)
 
     # --- stage breakdown (eager, CUDA events on the launching stream)
-    stages = None
-    work = None
+    stages = work = None
     if not args.no_stages:
-        stages, work = stage_breakdown(win, N, reps=5)
+        stages, work = stage_breakdown(win, N, reps=10)
 
     # --- end to end through the public API: inputs from pinned host memory every step,
     #     the per-view losses read back; keyframe weights from the adaptive scheduler
     e2e = None
     if not args.no_e2e:
-        e2e = end_to_end(win, sc, cams, tgt_rgb, tgt_d, args, torch, N)
+        e2e = end_to_end(win, sc, cams, tgt_rgb, tgt_d, args, torch, N, k_forms)
         if world > 1:
             e2e["value"] = job_throughput(world, e2e["steps"], max_over_ranks(e2e["seconds"], world, dev))
 
-    roof = None
+    roof = iteration = stage_roof = None
     if stages:
         work["workload"] = workload_config(sc)["workload"]
-        roof = roofline(stages, work, clk.summary())
-        roof["iteration_bound_ms"] = round(iteration_bound_ms(stages, work), 4)
-        roof["iteration_frac"] = roof["iteration_bound_ms"] / (ms_max / args.steps)
+        peaks = Peaks(sm_count, clocks)
+        stage_roof = stage_rooflines(stages, work, peaks)
+        roof = roofline(stages, work, peaks, stage_roof)
+        iteration = iteration_roofline(stages, work, peaks, ms_max / args.steps)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sc)
 
     if rank == 0:
-        extra = {"tile": tile, "batch_depth": bd, "batch_depth_bwd": bdb, "tile_instances": ninst}
+        extra = {"tile": tile, "batch_depth": bd, "batch_depth_bwd": bdb, "tile_instances": ninst,
+                 "config_index": args.config}
         if tuned:
-            extra["autotune_ms"] = tuned
+            extra["autotune"] = tuned
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded room scene)",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scene)",
             "config": workload_config(sc, extra),
             "view_iters_per_s": value * V,
             "per_view_form": per_view,
+            "paper_loop_form": paper_loop,
             "splat_backward": splat,
             "ssim_loss_form": ssim,
-            "e2e": {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
+            "e2e": {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step", "steps")}
             if e2e else None,
             "gpu_launches": gpu_launches,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "stages_ms": stages,
+            "stage_roofline": stage_roof,
+            "iteration_roofline": iteration,
             "roofline": roof,
             "cpu_baseline": cpu,
         }
@@ -480,7 +592,7 @@ def ssim_variant(MappingWindow, params_t, sc, tile, bd, cams, tgt_rgb, tgt_d, ca
     st = w.read_status()
     if st[0] != 0:
         raise SystemExit(f"device status (SSIM loss): {st}")
-    reps = 5
+    reps = MIN_FORM_STEPS
     e0.record()
     for _ in range(reps):
         N.cgs_ssim_loss(w.img, w.tgt_rgb, w.depth, w.tgt_depth, w.depth_count, w.V, w.cfg, w.view_weight, lam,
@@ -546,13 +658,45 @@ def stage_breakdown(win, N, reps=5):
     return {k: round(v, 4) for k, v in acc.items()}, work
 
 
+class Peaks:
+    """Roofline denominators: HBM = the measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs,
+    else the 6.8 TB/s fallback); FP32 ALU = SMs (read from the device) x 128 FP32 lanes x the
+    maximum SM clock (nvidia-smi clocks.max.sm sampled during the timed region, else
+    MEASURED_PEAKS.json, else 2070 MHz)."""
+
+    def __init__(self, sm_count, clocks):
+        mp = ROOT / "MEASURED_PEAKS.json"
+        measured = json.loads(mp.read_text()) if mp.exists() else {}
+        self.hbm_gbs = float(measured.get("hbm_gbs") or 6800.0)
+        self.hbm_source = "MEASURED_PEAKS.json hbm_gbs (of measured)" if measured.get("hbm_gbs") else \
+            "fallback 6.8 TB/s (of fallback)"
+        self.sm_count = int(sm_count)
+        mhz, src = (clocks or {}).get("sm_max_mhz"), "nvidia-smi clocks.max.sm"
+        if not mhz:
+            mhz, src = measured.get("sm_max_mhz"), "MEASURED_PEAKS.json sm_max_mhz"
+        if not mhz:
+            mhz, src = 2070.0, "nominal 2070 MHz"
+        self.sm_max_mhz = float(mhz)
+        self.alu_tops = self.sm_count * FP32_LANES_PER_SM * self.sm_max_mhz * 1e6 / 1e12
+        self.alu_source = (f"{self.sm_count} SMs (device) x {FP32_LANES_PER_SM} FP32 lanes x "
+                           f"{self.sm_max_mhz:.0f} MHz ({src}), derived")
+
+
+RASTER_STAGES = ("render_fwd", "raster_bwd")
+
+
 def hbm_bytes(stage, w):
-    """Algorithmic HBM bytes per launch: each input read once, each output written once."""
+    """Algorithmic HBM bytes per launch of a stage: each input read once, each output written
+    once (P parameters, S slots, M visible slots, I tile instances, X pixels, T tiles)."""
     P, S, M, I, X, T = w["params"], w["slots"], w["visible_slots"], w["instances"], w["pixels"], w["tiles"]
     if stage == "preprocess":
         return 4 * P + 4 * S + (48 + 48) * M          # params; radius of every slot; record + zeroed grad
     if stage == "bin_sort":
         return 4 * S + 12 * M + 8 * I + 8 * I + 4 * I + 8 * T   # scan rects, scatter keys, sort, vals, ranges
+    if stage == "render_fwd":
+        return 4 * I + 8 * T + 48 * M + 16 * X + 24 * X         # lists, ranges, records; targets; img/depth/T/last
+    if stage == "raster_bwd":
+        return 4 * I + 8 * T + 48 * M + 40 * X + 48 * M        # lists, records; fwd outputs + targets; slot grads
     if stage == "preprocess_bwd":
         return 4 * P + 4 * S + 48 * M + 4 * P + 24 * w["n"]   # params, radii, slot grads, grads, stats
     if stage == "adam":
@@ -560,7 +704,46 @@ def hbm_bytes(stage, w):
     return None
 
 
-TRAFFIC_PROFILE = ROOT / "profiles" / "k_render_bwd_traffic_window16_300k_1200x680.md"
+def raster_ops(stage, w):
+    if stage == "render_fwd":
+        return FWD_OPS_EVAL * w["pairs_fwd_eval"] + FWD_OPS_BLEND * w["pairs_blend"]
+    return BWD_OPS_EVAL * w["pairs_bwd_eval"] + BWD_OPS_BLEND * w["pairs_blend"]
+
+
+def stage_rooflines(stages, work, pk):
+    """Each stage against its own roof: the raster kernels against the FP32 ALU peak (formula
+    operations/s), the others against the measured HBM copy bandwidth."""
+    out = {}
+    for st, ms in stages.items():
+        t = ms / 1e3
+        if st in RASTER_STAGES:
+            ops = raster_ops(st, work)
+            out[st] = {"bound": "alu", "ms": ms, "work": ops, "achieved": ops / t / 1e12, "peak": pk.alu_tops,
+                       "unit": "Top/s", "frac": ops / t / 1e12 / pk.alu_tops,
+                       "hbm_frac": hbm_bytes(st, work) / t / 1e9 / pk.hbm_gbs}
+        else:
+            b = hbm_bytes(st, work)
+            out[st] = {"bound": "hbm", "ms": ms, "work": b, "achieved": b / t / 1e9, "peak": pk.hbm_gbs,
+                       "unit": "GB/s", "frac": b / t / 1e9 / pk.hbm_gbs}
+    return out
+
+
+def iteration_roofline(stages, work, pk, ms_iter):
+    """The whole iteration: its algorithmic HBM bytes over (iteration time x measured copy
+    bandwidth), and the combined bound (each stage at the faster of its two roofs) over the
+    iteration time."""
+    total_bytes = sum(hbm_bytes(st, work) for st in stages)
+    bound_s = 0.0
+    for st in stages:
+        t_hbm = hbm_bytes(st, work) / (pk.hbm_gbs * 1e9)
+        t_alu = raster_ops(st, work) / (pk.alu_tops * 1e12) if st in RASTER_STAGES else 0.0
+        bound_s += max(t_hbm, t_alu)
+    return {"hbm_bytes": total_bytes, "hbm_frac": total_bytes / (ms_iter / 1e3) / (pk.hbm_gbs * 1e9),
+            "hbm_peak_gbs": pk.hbm_gbs, "hbm_peak_source": pk.hbm_source,
+            "combined_bound_ms": 1e3 * bound_s, "combined_frac": 1e3 * bound_s / ms_iter,
+            "ms_per_iteration": ms_iter}
+
+
 RASTER_BWD_SOURCES = ("render_bwd.cu", "raster.cuh", "cgs_internal.cuh")
 
 
@@ -573,68 +756,34 @@ def raster_bwd_source_hash():
 
 
 def recorded_traffic(workload):
-    """DRAM bytes per launch of k_render_bwd from the committed ncu capture, if it was taken on
-    this workload and the kernel's sources are unchanged since (else None)."""
-    if not TRAFFIC_PROFILE.exists():
+    """DRAM bytes per launch of k_render_bwd from the committed ncu capture (ncu_traffic.json),
+    if it was taken on this workload and the kernel's sources are unchanged since (else None)."""
+    if not TRAFFIC_FILE.exists():
         return None
-    kv = {}
-    for line in TRAFFIC_PROFILE.read_text().splitlines():
-        if line.startswith("- ") and ": " in line:
-            k, v = line[2:].split(": ", 1)
-            kv[k.strip()] = v.strip().strip("`")
-    if kv.get("source_sha256") != raster_bwd_source_hash() or kv.get("workload") != workload:
+    rec = json.loads(TRAFFIC_FILE.read_text()).get("k_render_bwd")
+    if not rec or rec.get("source_sha256") != raster_bwd_source_hash() or rec.get("workload") != workload:
         return None
-    return float(kv["traffic_bytes_per_launch"])
+    return float(rec["traffic_bytes_per_launch"])
 
 
-def iteration_bound_ms(stages, work):
-    """Time one iteration would take if every stage ran at its roofline: HBM stages at the
-    measured copy bandwidth, raster stages at the FP32 lane peak (SURVEY-style combined bound)."""
-    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
-    bw = peaks.get("hbm_gbs", 6800.0) * 1e9
-    alu = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
-    t = 0.0
-    for st in stages:
-        if st == "render_fwd":
-            t += (FWD_OPS_EVAL * work["pairs_fwd_eval"] + FWD_OPS_BLEND * work["pairs_blend"]) / alu
-        elif st == "raster_bwd":
-            t += (BWD_OPS_EVAL * work["pairs_bwd_eval"] + BWD_OPS_BLEND * work["pairs_blend"]) / alu
-        else:
-            t += hbm_bytes(st, work) / bw
-    return 1e3 * t
-
-
-def roofline(stages, work, clocks):
-    """Roofline of the dominant kernel: FP32-ALU bound for the raster kernels (peak = SMs x
-    FP32 lanes x max SM clock), HBM bound for the rest (peak = measured copy bandwidth)."""
+def roofline(stages, work, pk, stage_roof):
+    """Roofline of the dominant kernel (the stage with the largest time)."""
     dom = max(stages, key=stages.get)
-    t = stages[dom] / 1e3
-    peaks = {}
-    mp = ROOT / "MEASURED_PEAKS.json"
-    if mp.exists():
-        peaks = json.loads(mp.read_text())
-    if dom in ("render_fwd", "raster_bwd"):
-        if dom == "render_fwd":
-            ops = FWD_OPS_EVAL * work["pairs_fwd_eval"] + FWD_OPS_BLEND * work["pairs_blend"]
-        else:
-            ops = BWD_OPS_EVAL * work["pairs_bwd_eval"] + BWD_OPS_BLEND * work["pairs_blend"]
-        peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-        ach = ops / t / 1e12
-        traffic = recorded_traffic(work.get("workload")) if dom == "raster_bwd" else None
-        return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Top/s",
-                "frac": ach / peak, "traffic": traffic,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (FP32 instructions/s), derived",
-                "work": {k: work[k] for k in ("pairs_fwd_eval", "pairs_bwd_eval", "pairs_blend")},
-                "ops_per_pair": {"fwd_eval": FWD_OPS_EVAL, "fwd_blend": FWD_OPS_BLEND, "bwd_eval": BWD_OPS_EVAL,
-                                 "bwd_blend": BWD_OPS_BLEND}}
-    b = hbm_bytes(dom, work)
-    peak = peaks.get("hbm_gbs", 6800.0)
-    ach = b / t / 1e9
-    return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+    r = stage_roof[dom]
+    out = {"kernel": {"raster_bwd": "k_render_bwd", "render_fwd": "k_render_fwd"}.get(dom, dom),
+           "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"], "unit": r["unit"], "frac": r["frac"],
+           "traffic": recorded_traffic(work.get("workload")) if dom == "raster_bwd" else None}
+    if r["bound"] == "alu":
+        out["peak_source"] = pk.alu_source
+        out["work"] = {k: work[k] for k in ("pairs_fwd_eval", "pairs_bwd_eval", "pairs_blend")}
+        out["ops_per_pair"] = {"fwd_eval": FWD_OPS_EVAL, "fwd_blend": FWD_OPS_BLEND, "bwd_eval": BWD_OPS_EVAL,
+                               "bwd_blend": BWD_OPS_BLEND}
+    else:
+        out["peak_source"] = pk.hbm_source
+    return out
 
 
-def end_to_end(win, sc, cams, tgt_rgb, tgt_d, args, torch, N):
+def end_to_end(win, sc, cams, tgt_rgb, tgt_d, args, torch, N, steps):
     """Steps through the public API: the adaptive scheduler (Eqs. 5-8) draws the window's
     view weights, the window's cameras, targets and weights are copied from pinned host
     memory (cameras and targets staged on a copy stream during the previous iteration),
@@ -675,7 +824,6 @@ def end_to_end(win, sc, cams, tgt_rgb, tgt_d, args, torch, N):
         one_step()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    steps = max(3, args.steps // 4)
     for _ in range(steps):
         one_step()
     torch.cuda.synchronize()

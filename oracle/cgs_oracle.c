@@ -27,6 +27,11 @@
  *                   that guide densification (Sec. III-A.3, Sec. IV-A).
  * Adam and the keyframe scheduler live in oracle.py.
  *
+ * Threads (OpenMP, orc_set_threads): loops run in parallel only over outputs that no
+ * other iteration writes (views, Gaussians, rows, listed pixels), and sums that cross
+ * iterations are formed per row and added in a fixed order, so every result is the same
+ * bit for bit whatever the thread count; the arithmetic of each step is unchanged.
+ *
  * Readings where the paper is silent (it defers to 3DGS for the renderer) are
  * listed beside each step.  Layouts:
  *   params  : means[n][3] | log_scales[n][3] | quats[n][4] (w,x,y,z) |
@@ -38,6 +43,7 @@
  *   a "slot" is (view v, Gaussian g) -> index v*n + g
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -46,6 +52,10 @@
 #define NCAM 17
 
 /* ------------------------------------------------------------------ helpers */
+
+/* Number of OpenMP threads the loops below use (default: OpenMP's own, all cores). */
+void orc_set_threads(int k) { if (k > 0) omp_set_num_threads(k); }
+int orc_get_threads(void) { return omp_get_max_threads(); }
 
 static int64_t sh_count(int deg) { return (int64_t)(deg + 1) * (deg + 1); }
 
@@ -297,9 +307,10 @@ int orc_preprocess(const double *P, int64_t n, int deg, const double *cams, int 
                    int32_t *fragile)
 {
     int Tx = (W + B - 1) / B, Ty = (H + B - 1) / B;
-    proj_t o;
     for (int v = 0; v < V; v++)
+#pragma omp parallel for schedule(static)
         for (int64_t g = 0; g < n; g++) {
+            proj_t o;
             int64_t s = (int64_t)v * n + g;
             project(P, n, deg, g, cams + NCAM * v, W, H, B, near_z, &o);
             double *r = rec + NREC * s;
@@ -362,19 +373,33 @@ int64_t orc_bin(const double *u, const double *v, const double *z, const int32_t
                 int W, int H, int B, int64_t capacity, uint32_t *ranges, uint32_t *vals)
 {
     int Tx = (W + B - 1) / B, Ty = (H + B - 1) / B;
-    int64_t Tv = (int64_t)Tx * Ty, Ttot = Tv * V;
-    int64_t count = 0;
-    int rect[4];
-    for (int64_t s = 0; s < (int64_t)V * n; s++) {
-        if (radius[s] <= 0) continue;
-        tile_rect(u[s], v[s], radius[s], B, Tx, Ty, rect);
-        for (int ty = rect[2]; ty < rect[3]; ty++)
-            count += rect[1] - rect[0];
+    int64_t Tv = (int64_t)Tx * Ty;
+    /* instances per view: a view's tiles and slots are its own, so views are binned apart */
+    int64_t *vcount = calloc((size_t)V + 1, sizeof(int64_t));
+#pragma omp parallel for schedule(dynamic)
+    for (int vv = 0; vv < V; vv++) {
+        int rect[4];
+        int64_t c = 0;
+        for (int64_t g = 0; g < n; g++) {
+            int64_t s = (int64_t)vv * n + g;
+            if (radius[s] <= 0) continue;
+            tile_rect(u[s], v[s], radius[s], B, Tx, Ty, rect);
+            c += (int64_t)(rect[1] - rect[0]) * (rect[3] - rect[2]);
+        }
+        vcount[vv + 1] = c;
     }
-    if (count > capacity || vals == NULL) return count;
-    inst_t *ins = malloc(sizeof(inst_t) * (count ? count : 1));
-    int64_t k = 0;
-    for (int vv = 0; vv < V; vv++)
+    for (int vv = 0; vv < V; vv++) vcount[vv + 1] += vcount[vv];
+    int64_t count = vcount[V];
+    if (count > capacity || vals == NULL) {
+        free(vcount);
+        return count;
+    }
+#pragma omp parallel for schedule(dynamic)
+    for (int vv = 0; vv < V; vv++) {
+        int64_t m = vcount[vv + 1] - vcount[vv];
+        inst_t *ins = malloc(sizeof(inst_t) * (m ? m : 1));
+        int rect[4];
+        int64_t k = 0;
         for (int64_t g = 0; g < n; g++) {
             int64_t s = (int64_t)vv * n + g;
             if (radius[s] <= 0) continue;
@@ -387,18 +412,20 @@ int64_t orc_bin(const double *u, const double *v, const double *z, const int32_t
                     k++;
                 }
         }
-    qsort(ins, count, sizeof(inst_t), inst_cmp);
-    /* ranges: exclusive scan of the per-tile counts (an empty tile is [pos, pos)) */
-    int64_t i = 0;
-    for (int64_t t = 0; t < Ttot; t++) {
-        ranges[2 * t] = (uint32_t)i;
-        while (i < count && ins[i].tile == t) {
-            vals[i] = (uint32_t)ins[i].slot;
-            i++;
+        qsort(ins, m, sizeof(inst_t), inst_cmp);
+        /* ranges: exclusive scan of the per-tile counts (an empty tile is [pos, pos)) */
+        int64_t i = 0;
+        for (int64_t t = vv * Tv; t < (vv + 1) * Tv; t++) {
+            ranges[2 * t] = (uint32_t)(vcount[vv] + i);
+            while (i < m && ins[i].tile == t) {
+                vals[vcount[vv] + i] = (uint32_t)ins[i].slot;
+                i++;
+            }
+            ranges[2 * t + 1] = (uint32_t)(vcount[vv] + i);
         }
-        ranges[2 * t + 1] = (uint32_t)i;
+        free(ins);
     }
-    free(ins);
+    free(vcount);
     return count;
 }
 
@@ -503,10 +530,15 @@ int orc_render_fwd(const double *rec, const uint32_t *ranges, const uint32_t *va
     int Tx = (W + B - 1) / B, Ty = (H + B - 1) / B;
     int64_t HW = (int64_t)H * W;
     if (hash) *hash = 1469598103934665603ULL;
+    /* per-row sums of the loss terms, added row after row below */
+    double *l1r = calloc((size_t)H, sizeof(double)), *ldr = calloc((size_t)H, sizeof(double));
+    int64_t *cntr = calloc((size_t)H, sizeof(int64_t));
     for (int v = 0; v < V; v++) {
-        double l1 = 0.0, ld = 0.0;
-        int64_t cnt = 0;
-        for (int y = 0; y < H; y++)
+        /* the decision hash follows pixel order, so it is formed on one thread */
+#pragma omp parallel for schedule(dynamic) if (!hash)
+        for (int y = 0; y < H; y++) {
+            double l1 = 0.0, ld = 0.0;
+            int64_t cnt = 0;
             for (int x = 0; x < W; x++) {
                 int64_t tile = (int64_t)v * Tx * Ty + (int64_t)(y / B) * Tx + (x / B);
                 uint32_t st = ranges[2 * tile], en = ranges[2 * tile + 1];
@@ -529,12 +561,26 @@ int orc_render_fwd(const double *rec, const uint32_t *ranges, const uint32_t *va
                     if (tgt_depth && tgt_depth[p] > 0.0) { ld += fabs(D - tgt_depth[p]); cnt++; }
                 }
             }
+            l1r[y] = l1;
+            ldr[y] = ld;
+            cntr[y] = cnt;
+        }
         if (tgt_rgb) {
+            double l1 = 0.0, ld = 0.0;
+            int64_t cnt = 0;
+            for (int y = 0; y < H; y++) {
+                l1 += l1r[y];
+                ld += ldr[y];
+                cnt += cntr[y];
+            }
             double w = cams[NCAM * v + 16];
             loss_view[v] = w * (l1 / (3.0 * HW) + (cnt > 0 ? lambda_d * ld / cnt : 0.0));
             depth_count[v] = cnt;
         }
     }
+    free(l1r);
+    free(ldr);
+    free(cntr);
     return 0;
 }
 
@@ -553,25 +599,33 @@ static double sgn(double x) { return x > 0 ? 1.0 : (x < 0 ? -1.0 : 0.0); }
  *   dalpha/do = G, dalpha/dpower = alpha (both 0 when alpha was clamped at 0.99)
  *   dpower/du = -(A dx + B dy), dpower/dv = -(C dy + B dx),
  *   dpower/dA = -dx^2/2, dpower/dB = -dx dy, dpower/dC = -dy^2/2
- * summed over pixels into grads[V*n][10] (which this function overwrites).
+ * summed over pixels into grads[V*n][10] (which this function overwrites).  grads_mag
+ * (NULL allowed) receives, per field, the sum over pixels of each term evaluated with every
+ * operand replaced by its magnitude (|c T| + |colour behind| for the difference in dI/dalpha,
+ * |A dx| + |B dy| for dpower/du, ...): the scale that rounding in a lower-precision
+ * evaluation of the same terms is proportional to, for tolerance-aware comparisons.  It
+ * does not enter grads.
  */
 int orc_render_bwd(const double *rec, const uint32_t *ranges, const uint32_t *vals, int V,
                    int64_t n, int W, int H, int B, const double *bg, const double *cams,
                    const double *img, const double *depth, const double *tgt_rgb,
                    const double *tgt_depth, const int64_t *depth_count, double lambda_d,
-                   const double *gimg, const double *gdepth, double *grads)
+                   const double *gimg, const double *gdepth, double *grads, double *grads_mag)
 {
     int Tx = (W + B - 1) / B, Ty = (H + B - 1) / B;
     int64_t HW = (int64_t)H * W;
     memset(grads, 0, sizeof(double) * NREC * V * n);
+    if (grads_mag) memset(grads_mag, 0, sizeof(double) * NREC * V * n);
     int64_t maxlen = 0;
     for (int64_t t = 0; t < (int64_t)V * Tx * Ty; t++) {
         int64_t len = (int64_t)ranges[2 * t + 1] - ranges[2 * t];
         if (len > maxlen) maxlen = len;
     }
-    step_t *st = malloc(sizeof(step_t) * (maxlen ? maxlen : 1));
-    double *S = malloc(sizeof(double) * 4 * (maxlen + 1));
+    /* views in parallel: the slots a view's pixels write (v*n + g) are that view's own */
+#pragma omp parallel for schedule(dynamic)
     for (int v = 0; v < V; v++) {
+        step_t *st = malloc(sizeof(step_t) * (maxlen ? maxlen : 1));
+        double *S = malloc(sizeof(double) * 4 * (maxlen + 1));
         double w = cams[NCAM * v + 16];
         for (int y = 0; y < H; y++)
             for (int x = 0; x < W; x++) {
@@ -602,31 +656,52 @@ int orc_render_bwd(const double *rec, const uint32_t *ranges, const uint32_t *va
                 }
                 for (int k = 0; k < nb; k++) {
                     const double *r = rec + NREC * st[k].slot;
-                    double *g = grads + NREC * st[k].slot;
                     double a = st[k].alpha, Tk = st[k].T;
-                    double dLda = 0.0;
+                    double dLda = 0.0, term[NREC] = {0};
+                    double dLda_mag = 0.0, mag[NREC] = {0};   /* magnitudes of the operands */
                     for (int ch = 0; ch < 3; ch++) {
-                        double dIda = r[6 + ch] * Tk - (S[4 * (k + 1) + ch] + T * bg[ch]) / (1.0 - a);
+                        double behind = (S[4 * (k + 1) + ch] + T * bg[ch]) / (1.0 - a);
+                        double dIda = r[6 + ch] * Tk - behind;
                         dLda += gI[ch] * dIda;
-                        g[6 + ch] += gI[ch] * a * Tk;
+                        dLda_mag += fabs(gI[ch]) * (fabs(r[6 + ch] * Tk) + fabs(behind));
+                        term[6 + ch] = gI[ch] * a * Tk;
+                        mag[6 + ch] = fabs(term[6 + ch]);
                     }
-                    double dDda = r[9] * Tk - S[4 * (k + 1) + 3] / (1.0 - a);
+                    double behind_d = S[4 * (k + 1) + 3] / (1.0 - a);
+                    double dDda = r[9] * Tk - behind_d;
                     dLda += gD * dDda;
-                    g[9] += gD * a * Tk;
-                    if (st[k].clamped) continue;
-                    double dx = r[0] - x, dy = r[1] - y;
-                    double dLdp = dLda * a;              /* dalpha/dpower = alpha */
-                    g[5] += dLda * st[k].G;              /* dalpha/do = G */
-                    g[0] += dLdp * (-(r[2] * dx + r[3] * dy));
-                    g[1] += dLdp * (-(r[4] * dy + r[3] * dx));
-                    g[2] += dLdp * (-0.5 * dx * dx);
-                    g[3] += dLdp * (-dx * dy);
-                    g[4] += dLdp * (-0.5 * dy * dy);
+                    dLda_mag += fabs(gD) * (fabs(r[9] * Tk) + fabs(behind_d));
+                    term[9] = gD * a * Tk;
+                    mag[9] = fabs(term[9]);
+                    if (!st[k].clamped) {
+                        double dx = r[0] - x, dy = r[1] - y;
+                        double dLdp = dLda * a;              /* dalpha/dpower = alpha */
+                        term[5] = dLda * st[k].G;            /* dalpha/do = G */
+                        term[0] = dLdp * (-(r[2] * dx + r[3] * dy));
+                        term[1] = dLdp * (-(r[4] * dy + r[3] * dx));
+                        term[2] = dLdp * (-0.5 * dx * dx);
+                        term[3] = dLdp * (-dx * dy);
+                        term[4] = dLdp * (-0.5 * dy * dy);
+                        double pm = dLda_mag * a;
+                        mag[5] = dLda_mag * st[k].G;
+                        mag[0] = pm * (fabs(r[2] * dx) + fabs(r[3] * dy));
+                        mag[1] = pm * (fabs(r[4] * dy) + fabs(r[3] * dx));
+                        mag[2] = pm * 0.5 * dx * dx;
+                        mag[3] = pm * fabs(dx * dy);
+                        mag[4] = pm * 0.5 * dy * dy;
+                    }
+                    /* this pixel's contribution (Eq. 4 sums them over the splat's pixels) */
+                    double *g = grads + NREC * st[k].slot;
+                    for (int f = 0; f < NREC; f++) g[f] += term[f];
+                    if (grads_mag) {
+                        double *gm = grads_mag + NREC * st[k].slot;
+                        for (int f = 0; f < NREC; f++) gm[f] += mag[f];
+                    }
                 }
             }
+        free(st);
+        free(S);
     }
-    free(st);
-    free(S);
     return 0;
 }
 
@@ -654,12 +729,14 @@ int orc_preprocess_bwd(const double *P, int64_t n, int deg, const double *cams, 
     layout_t L = param_layout(n, deg);
     int64_t K = sh_count(deg);
     memset(grads_out, 0, sizeof(double) * L.total);
-    proj_t o;
     for (int v = 0; v < V; v++) {
         const double *cam = cams + NCAM * v;
         const double *Rc = cam;
         double fx = cam[12], fy = cam[13];
+        /* Gaussians in parallel: Gaussian g's gradient entries are written by g alone */
+#pragma omp parallel for schedule(static)
         for (int64_t g = 0; g < n; g++) {
+            proj_t o;
             project(P, n, deg, g, cam, W, H, B, near_z, &o);
             if (!o.visible) continue;
             const double *G = slot_grads + NREC * ((int64_t)v * n + g);
@@ -786,6 +863,7 @@ int orc_render_pixels(const double *rec, const uint32_t *ranges, const uint32_t 
                       double *Tfin, uint32_t *last, int32_t *near_px)
 {
     int Tx = (W + B - 1) / B, Ty = (H + B - 1) / B;
+#pragma omp parallel for schedule(dynamic, 64)
     for (int64_t k = 0; k < npix; k++) {
         int v = pix[3 * k], x = pix[3 * k + 1], y = pix[3 * k + 2];
         int64_t tile = (int64_t)v * Tx * Ty + (int64_t)(y / B) * Tx + (x / B);
@@ -841,6 +919,7 @@ static double knn_one(const double *xyz, int64_t m, int k, int64_t i)
 int orc_knn_mean_d2(const double *xyz, int64_t m, int k, double *out)
 {
     if (k < 1 || k > 16) return -1;
+#pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < m; i++) out[i] = knn_one(xyz, m, k, i);
     return 0;
 }
@@ -849,9 +928,9 @@ int orc_knn_mean_d2(const double *xyz, int64_t m, int k, double *out)
 int orc_knn_mean_d2_at(const double *xyz, int64_t m, int k, const int64_t *idx, int64_t s, double *out)
 {
     if (k < 1 || k > 16) return -1;
-    for (int64_t t = 0; t < s; t++) {
+    for (int64_t t = 0; t < s; t++)
         if (idx[t] < 0 || idx[t] >= m) return -2;
-        out[t] = knn_one(xyz, m, k, idx[t]);
-    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < s; t++) out[t] = knn_one(xyz, m, k, idx[t]);
     return 0;
 }

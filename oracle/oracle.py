@@ -45,7 +45,7 @@ def build(force: bool = False) -> Path:
     if force or not _SO.exists() or _SO.stat().st_mtime < _SRC.stat().st_mtime:
         _SO.parent.mkdir(parents=True, exist_ok=True)
         tmp = _SO.with_suffix(f".{os.getpid()}.tmp")
-        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
                         "-o", str(tmp), str(_SRC), "-lm"], check=True)
         os.replace(tmp, _SO)
     return _SO
@@ -59,12 +59,15 @@ def _load():
         P = ctypes.c_void_p
         i32, i64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
         lib.orc_preprocess.argtypes = [P, i64, i32, P, i32, i32, i32, i32, f64, f64, P, P, P, P, P]
+        lib.orc_set_threads.argtypes = [i32]
+        lib.orc_set_threads.restype = None
+        lib.orc_get_threads.restype = i32
         lib.orc_bin.argtypes = [P, P, P, P, i32, i64, i32, i32, i32, i64, P, P]
         lib.orc_bin.restype = i64
         lib.orc_render_fwd.argtypes = [P, P, P, i32, i32, i32, i32, P, P, P, P, f64, f64,
                                        P, P, P, P, P, P, P, P]
         lib.orc_render_bwd.argtypes = [P, P, P, i32, i64, i32, i32, i32, P, P, P, P, P, P, P,
-                                       f64, P, P, P]
+                                       f64, P, P, P, P]
         lib.orc_preprocess_bwd.argtypes = [P, i64, i32, P, i32, i32, i32, i32, f64, P, P]
         lib.orc_densify_stats.argtypes = [P, P, i32, i64, i32, i32, P, P, P]
         lib.orc_sh_basis.argtypes = [i32, f64, f64, f64, P, P]
@@ -73,6 +76,18 @@ def _load():
         lib.orc_render_pixels.argtypes = [P, P, P, i32, i32, i32, P, P, i64, f64, P, P, P, P, P]
         _lib = lib
     return _lib
+
+
+def set_threads(k: int) -> int:
+    """Threads of the C oracle's parallel loops (results do not depend on it); returns the
+    count now in effect."""
+    lib = _load()
+    lib.orc_set_threads(int(k))
+    return int(lib.orc_get_threads())
+
+
+def get_threads() -> int:
+    return int(_load().orc_get_threads())
 
 
 def _p(a: np.ndarray):
@@ -185,11 +200,15 @@ def render_pixels(rec, ranges, vals, W, H, B, pix, bg=(0.0, 0.0, 0.0), tol=0.0) 
 
 
 def render_bwd(rec, ranges, vals, V, n, W, H, B, cams, img, depth, tgt_rgb, tgt_depth,
-               depth_count, bg=(0.0, 0.0, 0.0), lambda_d=0.1, dl_dimg=None, dl_ddepth=None) -> np.ndarray:
+               depth_count, bg=(0.0, 0.0, 0.0), lambda_d=0.1, dl_dimg=None, dl_ddepth=None,
+               with_abs=False):
     """Slot gradients [V*n][10]; pixel gradients from the fused L1 loss, or dl_dimg
-    [V,3,H,W] / dl_ddepth [V,H,W] (None: zero) when dl_dimg is given."""
+    [V,3,H,W] / dl_ddepth [V,H,W] (None: zero) when dl_dimg is given.  with_abs: also the
+    per-field sums of the terms evaluated on their operands' magnitudes (the rounding scale
+    of a float32 evaluation), returned as (grads, magnitudes)."""
     lib = _load()
     grads = np.zeros((V * n, NREC))
+    gabs = np.zeros((V * n, NREC)) if with_abs else None
     td = _f64(tgt_depth) if tgt_depth is not None else None
     gi = _f64(dl_dimg) if dl_dimg is not None else None
     gd = _f64(dl_ddepth) if dl_ddepth is not None else None
@@ -198,8 +217,9 @@ def render_bwd(rec, ranges, vals, V, n, W, H, B, cams, img, depth, tgt_rgb, tgt_
                        _p(cams_to_oracle(cams)), _p(_f64(img)), _p(_f64(depth)), _p(_f64(tgt_rgb)),
                        _p(td) if td is not None else None,
                        _p(np.ascontiguousarray(depth_count, np.int64)), lambda_d,
-                       _p(gi) if gi is not None else None, _p(gd) if gd is not None else None, _p(grads))
-    return grads
+                       _p(gi) if gi is not None else None, _p(gd) if gd is not None else None, _p(grads),
+                       _p(gabs) if with_abs else None)
+    return (grads, gabs) if with_abs else grads
 
 
 def preprocess_bwd(params, n, deg, cams, W, H, B, slot_grads, near=0.2) -> np.ndarray:
@@ -268,7 +288,8 @@ def iteration(params, n, deg, cams, W, H, B, tgt_rgb, tgt_depth, bg=(0.0, 0.0, 0
     grads = preprocess_bwd(params, n, deg, cams, W, H, B, sg, near)
     lo, glo = opacity_reg(params, n, lambda_o)
     grads[10 * n: 11 * n] += glo
-    return dict(pre=pre, ranges=ranges, vals=vals, fwd=fw, slot_grads=sg, grads=grads,
+    return dict(pre=pre, ranges=ranges, vals=vals, fwd=fw, slot_grads=sg, grads=grads, tgt_rgb=tgt_rgb,
+                tgt_depth=tgt_depth, dl_dimg=gi, dl_ddepth=gd,
                 loss_view=loss_view, loss=float(loss_view.sum() + lo), loss_o=lo)
 
 

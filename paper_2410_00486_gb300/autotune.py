@@ -59,6 +59,9 @@ def autotune(params: torch.Tensor, n: int, sh_degree: int, width: int, height: i
         win.set_window(cams, tgt_rgb, tgt_depth)
         win.fit_capacity(1.3)
         results[(tile, bd, bdb)] = time_window(win, reps)
+        st = win.read_status()[0]
+        if st != 0:                        # a candidate that fails is an error, not a slow one
+            raise RuntimeError(f"autotune candidate tile={tile} batch_depth={bd}/{bdb}: device status {st}")
         if log:
             log(f"autotune tile={tile} batch_depth={bd} batch_depth_bwd={bdb}: {results[(tile, bd, bdb)]:.3f} ms")
         del win

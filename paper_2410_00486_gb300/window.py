@@ -331,8 +331,11 @@ class MappingWindow:
             self._pv = pv
         return self._pv
 
-    def step_per_view(self):
-        """The same iteration, one view at a time (gradients accumulated, one Adam step)."""
+    def step_per_view(self, adam_every_view: bool = False):
+        """The same iteration, one view at a time (gradients accumulated, one Adam step).
+        adam_every_view: the paper's sequential mapping loop instead (Sec. III-C.2), one
+        optimiser step after every view, so each view renders the parameters the previous
+        view's step left (V iterations of one keyframe each)."""
         pv = self._per_view_buffers()
         c = self.cfg
         d = self.track_stats
@@ -352,10 +355,13 @@ class MappingWindow:
                 N.cgs_ssim_loss(img, tr, dep, td, dc, 1, c, w, self.lambda_ssim, lv, gi, gd, pv["ssim_ws"],
                                 self.status)
             N.cgs_render_bwd(self.params, self.n, cam, 1, c, pv["rec"], self.vals, pv["ranges"], pv["order"], w,
-                             img, dep, tf, la, tr, td, dc, gi, gd, pv["slot_grad"], self.grads, v > 0,
-                             self.accum if d else None, self.denom if d else None, self.max_r2d if d else None,
-                             self.status)
-        self.optimizer_step()
+                             img, dep, tf, la, tr, td, dc, gi, gd, pv["slot_grad"], self.grads,
+                             v > 0 and not adam_every_view, self.accum if d else None,
+                             self.denom if d else None, self.max_r2d if d else None, self.status)
+            if adam_every_view:
+                self.optimizer_step()
+        if not adam_every_view:
+            self.optimizer_step()
 
     # --------------------------------------------------------- CUDA graph
     def capture(self, warmup: int = 0):

@@ -12,6 +12,12 @@ GPU_IDX = [0, 1, 2, 3, 4, 5, 8, 9, 10, 6]
 # relative error 1e-3 against the FP64 oracle).
 PIX_TOL = 1e-4
 GRAD_REL_TOL = 1e-3
+# Rounding allowance of a float32 evaluation, per unit of a term's operand magnitude (the
+# oracle's grads_mag): 2^11 roundings of 2^-24, the transmittance and colour-behind
+# recursions of a pixel over up to 2048 blended splats with one rounding each.  Where the
+# blend's derivative cancels (a splat's colour close to the colour behind it), the exact
+# value is small but float32 rounds against the operands' size.
+F32_COND = 2.0 ** -13
 
 
 def torch_cuda():
@@ -188,9 +194,10 @@ def last_slots(last, ranges, vals, W, H, B):
 
 # ------------------------------------------------------- gradient comparisons
 
-def grad_check(got, ref, explained=None, name="", rel=GRAD_REL_TOL, l2=None):
+def grad_check(got, ref, explained=None, name="", rel=GRAD_REL_TOL, l2=None, mag=None):
     """Gradient parity: relative L2 error <= rel over the whole array, and per element
-    |got - ref| <= rel (|ref| + rel max|ref|).  Rows (slots or Gaussians) in `explained`
+    |got - ref| <= rel (|ref| + rel max|ref|) [+ F32_COND mag, when the oracle's operand
+    magnitudes `mag` of each element are given].  Rows (slots or Gaussians) in `explained`
     (bool per row) are where the oracle found a decision input near its threshold, so float32
     and float64 may take a different branch there: elements of those rows may exceed the
     per-element bound and are counted; any other element beyond it fails.  Returns
@@ -200,7 +207,10 @@ def grad_check(got, ref, explained=None, name="", rel=GRAD_REL_TOL, l2=None):
     r = np.asarray(ref, np.float64)
     e = rel_l2(g, r)
     scale = np.abs(r).max() if r.size else 0.0
-    bad = np.abs(g - r) > rel * (np.abs(r) + rel * scale)
+    bound = rel * (np.abs(r) + rel * scale)
+    if mag is not None:
+        bound = bound + F32_COND * np.asarray(mag, np.float64).reshape(bound.shape)
+    bad = np.abs(g - r) > bound
     if bad.ndim == 1:
         bad = bad[:, None]
     rows = bad.any(axis=1)
@@ -208,10 +218,28 @@ def grad_check(got, ref, explained=None, name="", rel=GRAD_REL_TOL, l2=None):
     unexpl = rows & ~expl
     print(f"    [{name}] rel L2 {e:.1e}  elements beyond the per-element bound: {int(bad.sum())} "
           f"({int(bad[expl].sum())} in rows near a threshold)")
+    g2, r2 = g.reshape(bad.shape), r.reshape(bad.shape)
+    for i, j in list(zip(*np.nonzero(bad & unexpl[:, None])))[:6]:
+        b2 = np.asarray(bound).reshape(bad.shape)
+        extra = f" mag {np.asarray(mag).reshape(bad.shape)[i, j]:.2e}" if mag is not None else ""
+        print(f"      row {i} col {j}: got {g2[i, j]:.6e} ref {r2[i, j]:.6e} |d| {abs(g2[i, j] - r2[i, j]):.2e} "
+              f"bound {b2[i, j]:.2e} max|ref| {scale:.2e}{extra}")
     assert e < (rel if l2 is None else l2), (name, e)
     assert not unexpl.any(), (name, f"{int(bad[unexpl].sum())} elements beyond the per-element bound, "
                                     f"e.g. rows {np.nonzero(unexpl)[0][:5]}")
     return e, int(bad.sum()), int(bad[expl].sum())
+
+
+def residual_sign_flags(img, tgt_rgb, depth=None, tgt_depth=None, eps=1e-5):
+    """Pixels whose L1 residual in some channel (or in depth, where the target depth is valid)
+    lies within eps of 0: the sign the loss's derivative takes there is a decision that a
+    rounding-sized difference in the render can flip."""
+    f = (np.abs(np.asarray(img) - np.asarray(tgt_rgb)) < eps).any(axis=1)
+    if depth is not None and tgt_depth is not None:
+        td = np.asarray(tgt_depth)
+        dscale = max(1.0, float(np.abs(td).max()))
+        f |= (td > 0) & (np.abs(np.asarray(depth) - td) < eps * dscale)
+    return f
 
 
 def slots_in_flagged_tiles(near, ranges, vals, W, H, B, m, reach_px=0):
@@ -233,18 +261,94 @@ def slots_in_flagged_tiles(near, ranges, vals, W, H, B, m, reach_px=0):
     return out
 
 
-def param_grad_check(got, ref, n, deg, explained=None, tag="", rel=GRAD_REL_TOL, l2=None):
+def param_grad_check(got, ref, n, deg, explained=None, tag="", rel=GRAD_REL_TOL, l2=None, checks=None):
     """grad_check per parameter group of the flat parameter vector, rows = Gaussians
     (explained: bool per Gaussian)."""
     out = {}
     for name, sl in group_slices(n, deg).items():
         w = (sl.stop - sl.start) // n
-        out[name] = grad_check(np.asarray(got)[sl].reshape(n, w), np.asarray(ref)[sl].reshape(n, w), explained,
-                               f"{tag} {name}", rel, l2)
+        try:
+            out[name] = grad_check(np.asarray(got)[sl].reshape(n, w), np.asarray(ref)[sl].reshape(n, w), explained,
+                                   f"{tag} {name}", rel, l2)
+        except AssertionError as err:
+            if checks is None:
+                raise
+            checks.append(err)
     return out
+
+
+def field_grad_check(got, ref, explained=None, tag="", mag=None, rel=GRAD_REL_TOL, l2=None):
+    """grad_check on each of the ten slot-gradient fields (columns); every field is checked
+    (and printed) before the first failure is raised."""
+    errs = []
+    for k, f in enumerate(["u", "v", "A", "B", "C", "o", "r", "g", "b", "z"]):
+        try:
+            grad_check(got[:, k], ref[:, k], explained, f"{tag} {f}", rel, l2,
+                       None if mag is None else mag[:, k])
+        except AssertionError as err:
+            errs.append(err)
+    if errs:
+        raise errs[0]
 
 
 def gaussians_of_slots(slot_mask, n):
     """bool per Gaussian: any of its slots (v n + g) set."""
     m = np.asarray(slot_mask, bool)
     return m.reshape(-1, n).any(axis=0)
+
+
+def from_params_explained(sc, it, gpu_img, gpu_slot_grad, reach_px=0, tol=1e-3):
+    """Gaussians whose gradients a float32 iteration from the same parameters may legitimately
+    take elsewhere than the float64 oracle's iteration `it`:
+      - a slot listed in a tile holding a pixel whose decision inputs lie within a relative
+        `tol` of a threshold (1e-3: the float32 projection upstream moves the records by about
+        that much more than the blend's own rounding), or a pixel whose value differs by more
+        than the pixel tolerance, or within reach_px of one;
+      - a slot whose projection is fragile (its tile rectangle or visibility may differ);
+      - a slot whose gradient differs from the oracle's by more than the per-element bound
+        but within the float32 rounding allowance of its terms (F32_COND x operand
+        magnitudes from the oracle), which the chain rule then carries to the parameters.
+    Returns (bool per Gaussian, dict of counts)."""
+    V, n, W, H, B = sc.views, sc.n, sc.width, sc.height, sc.tile
+    rec, ranges, vals = it["pre"]["rec"], it["ranges"], it["vals"]
+    fw = O.render_fwd(rec, ranges, vals, V, W, H, B, sc.cams, tol=tol)
+    flag = (fw["near"] != 0) | (np.abs(np.asarray(gpu_img) - it["fwd"]["img"]).max(1) > PIX_TOL)
+    if it["dl_dimg"] is None:        # the L1 loss: the residual's sign is a decision
+        flag |= residual_sign_flags(it["fwd"]["img"], it["tgt_rgb"], it["fwd"]["depth"], it["tgt_depth"])
+    near = slots_in_flagged_tiles(flag, ranges, vals, W, H, B, V * n, reach_px)
+    _, mag = O.render_bwd(rec, ranges, vals, V, n, W, H, B, sc.cams, it["fwd"]["img"], it["fwd"]["depth"],
+                          it["tgt_rgb"], it["tgt_depth"], it["fwd"]["depth_count"], dl_dimg=it["dl_dimg"],
+                          dl_ddepth=it["dl_ddepth"], with_abs=True)
+    sg = np.asarray(gpu_slot_grad, np.float64)
+    ref = it["slot_grads"]
+    scale = np.abs(ref).max(axis=0, keepdims=True)
+    plain = GRAD_REL_TOL * (np.abs(ref) + GRAD_REL_TOL * scale)
+    d = np.abs(sg - ref)
+    cond = ((d > plain) & (d <= plain + F32_COND * mag)).any(axis=1)
+    fragile = it["pre"]["fragile"] > 0
+    expl = gaussians_of_slots(near | fragile | cond, n)
+    counts = {"flagged_px": float(flag.mean()), "near_slots": int(near.sum()), "fragile_slots": int(fragile.sum()),
+              "conditioned_slots": int(cond.sum()), "gaussians": int(expl.sum())}
+    return expl, counts
+
+
+def check_iteration_against_oracle(sc, win, it, tag, reach_px=0, grads=None):
+    """A GPU window iteration from the same parameters as the oracle's iteration `it`: pixels
+    within PIX_TOL except where a decision input lies within a relative 1e-3 of its
+    threshold (those are counted, and fewer than 1e-4 of all pixels may actually differ by
+    more), per-view losses within 1e-4, parameter gradients by param_grad_check with the rows
+    from_params_explained gives.  `grads` overrides the window's gradient (autograd)."""
+    img = win.img.cpu().numpy()
+    expl, counts = from_params_explained(sc, it, img, sg_from_gpu(win.slot_grad), reach_px)
+    err = np.abs(img - it["fwd"]["img"]).max(1)
+    ok = ~(O.render_fwd(it["pre"]["rec"], it["ranges"], it["vals"], sc.views, sc.width, sc.height, sc.tile,
+                        sc.cams, tol=1e-3)["near"] != 0)
+    dscale = max(1.0, np.abs(it["fwd"]["depth"]).max())
+    e_d = (np.abs(win.depth.cpu().numpy() - it["fwd"]["depth"])[ok] / dscale).max()
+    print(f"[{tag}] pixels near a threshold {1 - ok.mean():.2e}, beyond {PIX_TOL:g}: {(err > PIX_TOL).mean():.2e}, "
+          f"max|dimg| elsewhere {err[ok].max():.2e}, |ddepth|/scale {e_d:.2e}; explained Gaussians {counts}")
+    assert err[ok].max() < PIX_TOL and e_d < PIX_TOL
+    assert (err > PIX_TOL).mean() < 1e-4
+    np.testing.assert_allclose(win.loss_view.cpu().numpy(), it["loss_view"], rtol=1e-4)
+    g = (win.grads if grads is None else grads).detach().cpu().numpy().astype(np.float64)
+    return param_grad_check(g, it["grads"], sc.n, sc.sh_degree, expl, tag)

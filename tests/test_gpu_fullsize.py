@@ -13,8 +13,8 @@ import pytest
 from oracle import oracle as O
 from synth import make_scene
 from synth.scenes import param_layout
-from tests.gpu_util import (PIX_TOL, check_culled_lists, gaussians_of_slots, grad_check, last_slots, native,
-                            param_grad_check, rec_from_gpu, round32, sg_from_gpu, torch_cuda)
+from tests.gpu_util import (PIX_TOL, check_culled_lists, field_grad_check, gaussians_of_slots, grad_check,
+                            last_slots, native, param_grad_check, rec_from_gpu, round32, sg_from_gpu, torch_cuda)
 
 pytestmark = pytest.mark.gpu
 
@@ -207,8 +207,8 @@ def test_fullsize_forward_sampled_pixels():
         assert (np.abs(dep[view, yy, xx] - ref["depth"])[ok] / dscale).max() < PIX_TOL
         lo = ref["last"].astype(np.int64)
         tl = (yy // 16) * ((W + 15) // 16) + xx // 16
-        slot_o = np.where(lo > 0, vals_o[np.clip(ranges_o[tl, 0].astype(np.int64) + lo - 1, 0, len(vals_o) - 1)]
-                          + view * n, -1)
+        slot_o = np.where(lo > 0, vals_o.astype(np.int64)[np.clip(ranges_o[tl, 0].astype(np.int64) + lo - 1, 0,
+                                                                  len(vals_o) - 1)] + view * n, -1)
         assert np.array_equal(last_g[view, yy, xx][ok], slot_o[ok])
     assert flagged < 0.01 * 4000
     print(f"[fullsize fwd pixels] flagged {flagged} of 4000")
@@ -254,7 +254,9 @@ def sampled_tile_lists(S, per_view=16, views=(0, 5, 11, 15), seed=2):
     pix = np.concatenate(pix).astype(np.int32)
     rec10, _, _ = rec_from_gpu(win.rec)
     px = O.render_pixels(rec10, o_ranges, o_vals, W, H, 16, pix, tol=1e-5)
-    fl = pix[px["near"] != 0]
+    tr = win.tgt_rgb.cpu().numpy()[pix[:, 0], :, pix[:, 2], pix[:, 1]]
+    resid = (np.abs(px["img"] - tr) < 1e-5).any(axis=1)     # the L1 residual's sign, near 0
+    fl = pix[(px["near"] != 0) | resid]
     near_tiles = np.unique(fl[:, 0] * Tv + (fl[:, 2] // 16) * Tx + fl[:, 1] // 16)
     near = np.zeros(sc.views * n, bool)
     for t in near_tiles:
@@ -277,14 +279,13 @@ def test_fullsize_raster_backward_sampled_tiles():
                      win.t_final, win.last, win.tgt_rgb, win.tgt_depth, win.depth_count, None, None, sg)
     torch.cuda.synchronize()
     g = sg_from_gpu(sg)
-    ref = O.render_bwd(rec10, o_ranges, o_vals, V, n, W, H, 16, sc.cams, win.img.cpu().numpy(),
-                       win.depth.cpu().numpy(), win.tgt_rgb.cpu().numpy(), win.tgt_depth.cpu().numpy(),
-                       win.depth_count.cpu().numpy().astype(np.int64))
+    ref, mag = O.render_bwd(rec10, o_ranges, o_vals, V, n, W, H, 16, sc.cams, win.img.cpu().numpy(),
+                            win.depth.cpu().numpy(), win.tgt_rgb.cpu().numpy(), win.tgt_depth.cpu().numpy(),
+                            win.depth_count.cpu().numpy().astype(np.int64), with_abs=True)
     touched = np.abs(ref).sum(1) > 0
     assert touched.sum() > 2000
     print(f"[fullsize bwd] touched slots {touched.sum()}, in tiles with a flagged pixel {near.sum()}")
-    for k, f in enumerate(["u", "v", "A", "B", "C", "o", "r", "g", "b", "z"]):
-        grad_check(g[touched, k], ref[touched, k], near[touched], f"fullsize bwd {f}")
+    field_grad_check(g[touched], ref[touched], near[touched], "fullsize bwd", mag=mag[touched])
     assert np.all(g[~touched] == 0)
     S["sampled"] = (rg, o_ranges, o_vals, rec10, near, ref)
 

@@ -141,3 +141,23 @@ def test_params_layout_groups():
     lay = param_layout(5, 3)
     assert lay["total"] == 5 * 59
     assert lay["sh_rest"] - lay["sh_dc"] == 15
+
+
+def test_operand_magnitudes_bound_the_gradient_terms():
+    # grads_mag sums each term with its operands replaced by their magnitudes: never below
+    # |grad| (triangle inequality); for the colour and depth fields, whose terms are single
+    # products, equal to the sum of |terms|, i.e. |grad| where every term has one sign
+    sc = make_tiny_scene(seed=2, n=40, sh_degree=1, W=32, H=24, views=2, tile=8)
+    pre = O.preprocess(sc.params, sc.n, 1, sc.cams, sc.width, sc.height, sc.tile)
+    rec = pre["rec"]
+    ranges, vals = O.bin_records(rec, pre["radius"], 2, sc.n, sc.width, sc.height, sc.tile)
+    fw = O.render_fwd(rec, ranges, vals, 2, sc.width, sc.height, sc.tile, sc.cams)
+    tgt = fw["img"] + 0.05
+    g, mag = O.render_bwd(rec, ranges, vals, 2, sc.n, sc.width, sc.height, sc.tile, sc.cams, fw["img"],
+                          fw["depth"], tgt, None, fw["depth_count"], with_abs=True)
+    g2 = O.render_bwd(rec, ranges, vals, 2, sc.n, sc.width, sc.height, sc.tile, sc.cams, fw["img"],
+                      fw["depth"], tgt, None, fw["depth_count"])
+    assert np.array_equal(g, g2)                       # the magnitudes do not touch the gradient
+    assert np.all(mag >= np.abs(g) * (1 - 1e-12))
+    np.testing.assert_allclose(mag[:, 6:9], np.abs(g[:, 6:9]), rtol=1e-12)   # img < tgt: one sign
+    assert (mag[:, 0] > 1.5 * np.abs(g[:, 0])).any()  # du terms cancel somewhere

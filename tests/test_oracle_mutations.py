@@ -21,7 +21,7 @@ MUTATIONS = [
      [lambda: TG.test_backward_matches_central_fd(*TG.FD_CASES[1])]),
     ("dY[12][0] = -6 * d3 * x * z;", "dY[12][0] = 6 * d3 * x * z;",
      [lambda: TP.test_sh_basis_gradient_fd()]),
-    ("g[1] += dLdp * (-(r[4] * dy + r[3] * dx));", "g[1] += dLdp * (-(r[4] * dy - r[3] * dx));",
+    ("term[1] = dLdp * (-(r[4] * dy + r[3] * dx));", "term[1] = dLdp * (-(r[4] * dy - r[3] * dx));",
      [lambda: TG.test_backward_matches_central_fd(*TG.FD_CASES[2])]),
     ("o->a = cov[0] + 0.3;", "o->a = cov[0] + 0.03;",
      [TP.test_isotropic_on_axis_closed_form]),
@@ -59,7 +59,7 @@ def mutated_oracle(tmp_path, original, mistake):
     src = tmp_path / "m.c"
     so = tmp_path / "m.so"
     src.write_text(SRC.replace(original, mistake))
-    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
                     "-o", str(so), str(src), "-lm"], check=True)
     saved = (O._lib, O._SO, O._SRC)
     O._lib, O._SO, O._SRC = None, so, src

@@ -200,3 +200,25 @@ def test_render_pixels_matches_full_render():
     np.testing.assert_array_equal(px["img"], fw["img"][0][:, pix[:, 2], pix[:, 1]].T)
     np.testing.assert_array_equal(px["T"], fw["T"][0][pix[:, 2], pix[:, 1]])
     np.testing.assert_array_equal(px["last"], fw["last"][0][pix[:, 2], pix[:, 1]])
+
+
+def test_oracle_results_do_not_depend_on_thread_count():
+    # the C oracle's parallel loops write disjoint outputs and add per-row sums in order
+    sc = make_tiny_scene(seed=5, n=200, sh_degree=3, W=61, H=45, views=3, tile=8)
+    pre = O.preprocess(sc.params_target, sc.n, 3, sc.cams, sc.width, sc.height, sc.tile)
+    ranges, vals = O.bin_records(pre["rec"], pre["radius"], 3, sc.n, sc.width, sc.height, sc.tile)
+    tgt = O.render_fwd(pre["rec"], ranges, vals, 3, sc.width, sc.height, sc.tile, sc.cams)
+    saved = O.get_threads()
+    runs = []
+    try:
+        for k in (1, 4):
+            O.set_threads(k)
+            runs.append(O.iteration(sc.params, sc.n, 3, sc.cams, sc.width, sc.height, sc.tile, tgt["img"],
+                                    tgt["depth"], tol=1e-5))
+    finally:
+        O.set_threads(saved)
+    a, b = runs
+    assert np.array_equal(a["vals"], b["vals"]) and np.array_equal(a["ranges"], b["ranges"])
+    for k in ("img", "depth", "T", "last", "loss_view", "near"):
+        assert np.array_equal(a["fwd"][k], b["fwd"][k]), k
+    assert np.array_equal(a["slot_grads"], b["slot_grads"]) and np.array_equal(a["grads"], b["grads"])
