@@ -216,9 +216,11 @@ int cgs_render_fwd_noalloc(const float *rec, const uint32_t *vals, const uint32_
  * cgs_raster_bwd -- backward of the blend (Eqs. 2-4, Sec. III-C.1), pixel-parallel,
  * back to front from `last`, with the transmittance recomputed from the stored
  * final T (T_j = T_{j+1} / (1 - alpha_j)) instead of stored per-pixel lists.  Per
- * blended (splat, pixel) pair, dL/d(u, v, A, B, C, opacity, rgb, depth); the 32
- * pixels of a warp are summed with shuffles before one set of atomic adds per
- * splat into slot_grad.  dL/dalpha is zero where alpha was clamped at 0.99.
+ * blended (splat, pixel) pair, dL/d(u, v, A, B, C, opacity, rgb, depth); the pixels
+ * of a warp are summed (in registers per thread, then across the warp through shared
+ * memory) before one set of atomic adds per splat into slot_grad, or added by each
+ * contributing lane directly when few lanes contribute.  dL/dalpha is zero where alpha
+ * was clamped at 0.99.
  * Pixel gradients come either from the fused L1 loss (dl_dimg == NULL: sign of the
  * residual, 0 at 0, times w_v / (3 H W) and w_v lambda_depth / depth_count) or
  * from the caller (dl_dimg float[V][3][H][W], dl_ddepth float[V][H][W] or NULL).
