@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--config", type=int, default=5)
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--batch-depth", type=int, default=128, help="splats per staged batch, forward")
-    ap.add_argument("--batch-depth-bwd", type=int, default=64, help="splats per staged batch, backward")
+    ap.add_argument("--batch-depth-bwd", type=int, default=32, help="splats per staged batch, backward")
     ap.add_argument("--autotune", action="store_true", help="pick tile/batch depth by measurement first")
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -627,7 +627,7 @@ def stage_breakdown(win, N, reps=5):
         ev[3].record()
         N.cgs_raster_bwd(win.rec, win.vals, win.ranges, win.order, win.V, c, win.view_weight, win.img, win.depth,
                          win.t_final, win.last, win.tgt_rgb, win.tgt_depth, win.depth_count, None, None,
-                         win.slot_grad, win.status)
+                         win.slot_grad, win.status, work=win.work)
         ev[4].record()
         N.cgs_preprocess_bwd(win.params, win.n, win.cams, win.V, c, win.rec, win.slot_grad, win.grads, False,
                              win.accum, win.denom, win.max_r2d, win.status)

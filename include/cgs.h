@@ -225,13 +225,19 @@ int cgs_render_fwd_noalloc(const float *rec, const uint32_t *vals, const uint32_
  * residual, 0 at 0, times w_v / (3 H W) and w_v lambda_depth / depth_count) or
  * from the caller (dl_dimg float[V][3][H][W], dl_ddepth float[V][H][W] or NULL).
  *   slot_grad  device in/out: accumulated (+=); zeroed by cgs_preprocess
+ *   work       device uint32[1] or NULL.  Given, the launch is persistent: as many blocks as
+ *              the GPU holds resident take the (view, tile) items, in tile_order, from this
+ *              counter (the call sets it to 0 first and leaves the number of items taken plus
+ *              the blocks in it).  NULL: one block per item.  Results are the same either way
+ *              up to float summation order; calls that share a counter must not overlap.
  */
 int cgs_raster_bwd(const float *rec, const uint32_t *vals, const uint32_t *ranges,
                    const uint32_t *tile_order, int32_t V, const cgs_config *cfg,
                    const float *view_weight, const float *img, const float *depth,
                    const float *t_final, const uint32_t *last, const float *tgt_rgb,
                    const float *tgt_depth, const int32_t *depth_count, const float *dl_dimg,
-                   const float *dl_ddepth, float *slot_grad, int32_t *status_dev, void *stream);
+                   const float *dl_ddepth, float *slot_grad, uint32_t *work, int32_t *status_dev,
+                   void *stream);
 
 /*
  * Splat-wise backward (Sec. III-C.1 and Fig. 4a: the paper's backward).  The forward
@@ -287,7 +293,7 @@ int cgs_render_bwd(const float *params, int64_t n, const cgs_camera *cams, int32
                    const uint32_t *last, const float *tgt_rgb, const float *tgt_depth,
                    const int32_t *depth_count, const float *dl_dimg, const float *dl_ddepth,
                    float *slot_grad, float *param_grad, int32_t accumulate, float *accum,
-                   float *denom, float *max_r2d, int32_t *status_dev, void *stream);
+                   float *denom, float *max_r2d, uint32_t *work, int32_t *status_dev, void *stream);
 
 /*
  * cgs_densify_stats -- per-Gaussian statistics that guide adaptive densification

@@ -72,11 +72,11 @@ _SIGS = {
     "cgs_raster_bwd_splat": (c_int32, [_P, _P, _P, _P, c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                        _P, c_int64, _P, _P, _P, _P]),
     "cgs_raster_bwd": (c_int32, [_P, _P, _P, _P, c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
-                                 _P, _P, _P]),
+                                 _P, _P, _P, _P]),
     "cgs_preprocess_bwd": (c_int32, [_P, c_int64, _P, c_int32, _P, _P, _P, _P, c_int32, _P, _P, _P,
                                      _P, _P]),
     "cgs_render_bwd": (c_int32, [_P, c_int64, _P, c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
-                                 _P, _P, _P, _P, _P, _P, c_int32, _P, _P, _P, _P, _P]),
+                                 _P, _P, _P, _P, _P, _P, c_int32, _P, _P, _P, _P, _P, _P]),
     "cgs_densify_stats": (c_int32, [_P, _P, c_int64, c_int32, _P, _P, _P, _P, _P]),
     "cgs_adam": (c_int32, [_P, _P, _P, _P, c_int64, c_int32, _P, c_float, c_float, c_float, c_int32,
                            _P, c_float, _P, _P]),
@@ -230,11 +230,11 @@ def cgs_raster_bwd_splat(rec, vals, ranges, tile_order, V, cfg, view_weight, img
 
 
 def cgs_raster_bwd(rec, vals, ranges, tile_order, V, cfg, view_weight, img, depth, t_final, last, tgt_rgb,
-                   tgt_depth, depth_count, dl_dimg, dl_ddepth, slot_grad, status=None, stream=None):
+                   tgt_depth, depth_count, dl_dimg, dl_ddepth, slot_grad, status=None, stream=None, work=None):
     _check("cgs_raster_bwd", lib().cgs_raster_bwd(
         _dev(rec), _dev(vals), _dev(ranges), _dev(tile_order), V, byref(cfg), _dev(view_weight), _dev(img),
         _dev(depth), _dev(t_final), _dev(last), _dev(tgt_rgb), _dev(tgt_depth), _dev(depth_count),
-        _dev(dl_dimg), _dev(dl_ddepth), _dev(slot_grad), _dev(status), _stream(stream)))
+        _dev(dl_dimg), _dev(dl_ddepth), _dev(slot_grad), _dev(work), _dev(status), _stream(stream)))
 
 
 def cgs_preprocess_bwd(params, n, cams, V, cfg, rec, slot_grad, param_grad, accumulate=False, accum=None,
@@ -246,12 +246,13 @@ def cgs_preprocess_bwd(params, n, cams, V, cfg, rec, slot_grad, param_grad, accu
 
 def cgs_render_bwd(params, n, cams, V, cfg, rec, vals, ranges, tile_order, view_weight, img, depth, t_final,
                    last, tgt_rgb, tgt_depth, depth_count, dl_dimg, dl_ddepth, slot_grad, param_grad,
-                   accumulate=False, accum=None, denom=None, max_r2d=None, status=None, stream=None):
+                   accumulate=False, accum=None, denom=None, max_r2d=None, status=None, stream=None, work=None):
     _check("cgs_render_bwd", lib().cgs_render_bwd(
         _dev(params), n, _dev(cams), V, byref(cfg), _dev(rec), _dev(vals), _dev(ranges), _dev(tile_order),
         _dev(view_weight), _dev(img), _dev(depth), _dev(t_final), _dev(last), _dev(tgt_rgb), _dev(tgt_depth),
         _dev(depth_count), _dev(dl_dimg), _dev(dl_ddepth), _dev(slot_grad), _dev(param_grad),
-        int(bool(accumulate)), _dev(accum), _dev(denom), _dev(max_r2d), _dev(status), _stream(stream)))
+        int(bool(accumulate)), _dev(accum), _dev(denom), _dev(max_r2d), _dev(work), _dev(status),
+        _stream(stream)))
 
 
 def cgs_densify_stats(rec, slot_grad, n, V, cfg, accum, denom, max_r2d, stream=None):

@@ -156,7 +156,7 @@ int cgs_raster_bwd(const float *rec, const uint32_t *vals, const uint32_t *range
                    int32_t V, const cgs_config *cfg, const float *view_weight, const float *img, const float *depth,
                    const float *t_final, const uint32_t *last, const float *tgt_rgb, const float *tgt_depth,
                    const int32_t *depth_count, const float *dl_dimg, const float *dl_ddepth, float *slot_grad,
-                   int32_t *status_dev, void *stream)
+                   uint32_t *work, int32_t *status_dev, void *stream)
 {
     (void)status_dev;
     if (!rec || !vals || !ranges || !t_final || !last || !slot_grad || !cfg_ok(cfg)) return CGS_ERR_ARG;
@@ -187,6 +187,7 @@ int cgs_raster_bwd(const float *rec, const uint32_t *vals, const uint32_t *range
     a.dl_dimg = dl_dimg;
     a.dl_ddepth = dl_ddepth;
     a.sgrad = slot_grad;
+    a.work = work;
     const int bd = cfg->batch_depth_bwd ? cfg->batch_depth_bwd : cfg->batch_depth;
     return cuda_status(raster_bwd(a, cfg->tile, bd, (cudaStream_t)stream));
 }
@@ -210,12 +211,12 @@ int cgs_render_bwd(const float *params, int64_t n, const cgs_camera *cams, int32
                    const float *view_weight, const float *img, const float *depth, const float *t_final,
                    const uint32_t *last, const float *tgt_rgb, const float *tgt_depth, const int32_t *depth_count,
                    const float *dl_dimg, const float *dl_ddepth, float *slot_grad, float *param_grad,
-                   int32_t accumulate, float *accum, float *denom, float *max_r2d, int32_t *status_dev,
-                   void *stream)
+                   int32_t accumulate, float *accum, float *denom, float *max_r2d, uint32_t *work,
+                   int32_t *status_dev, void *stream)
 {
     if (!params || !cams || !param_grad || !cfg_ok(cfg) || !sizes_ok(n, V, cfg)) return CGS_ERR_ARG;
     int st = cgs_raster_bwd(rec, vals, ranges, tile_order, V, cfg, view_weight, img, depth, t_final, last, tgt_rgb,
-                            tgt_depth, depth_count, dl_dimg, dl_ddepth, slot_grad, status_dev, stream);
+                            tgt_depth, depth_count, dl_dimg, dl_ddepth, slot_grad, work, status_dev, stream);
     if (st != CGS_OK) return st;
     return cgs_preprocess_bwd(params, n, cams, V, cfg, rec, slot_grad, param_grad, accumulate, accum, denom,
                               max_r2d, status_dev, stream);

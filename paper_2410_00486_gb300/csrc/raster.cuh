@@ -45,13 +45,15 @@ struct RasterBwdArgs {
     float lambda_d;
     const float *dl_dimg, *dl_ddepth;
     float *sgrad;
+    uint32_t *work;   // persistent launch: the work counter (null: one block per tile)
 };
 
-// Map a work item to (view, tile x, tile y).
+// Map a work item (a block index, or an item taken from a work counter) to (view, tile x,
+// tile y).
 __device__ __forceinline__ void item_tile(const uint32_t *order, const Grid &g, int64_t &tile, int &view, int &tx,
-                                          int &ty)
+                                          int &ty, uint32_t item)
 {
-    tile = order ? (int64_t)order[blockIdx.x] : (int64_t)blockIdx.x;
+    tile = order ? (int64_t)order[item] : (int64_t)item;
     view = (int)(tile / g.Tv);
     const int t = (int)(tile - (int64_t)view * g.Tv);
     ty = t / g.Tx;
@@ -94,11 +96,13 @@ __host__ __device__ constexpr int row_step()
 
 // Resident warps per SM each raster kernel is compiled for (__launch_bounds__ minimum
 // blocks): the register budget is 64K / (warps x 32).  The forward runs at 32 warps (64
-// registers, 56 used; 36 or 40 gain nothing).  The backward, with eight pixels of state
-// per thread, runs at 20 warps (96 registers, no spill); 18 spills a little and 22 or 24
-// spill hundreds of bytes, and both are slower.
+// registers, 56 used; 36 or 40 gain nothing).  The backward keeps the per-pixel loss
+// gradients in shared memory (read once per blended pixel) and runs at 28 warps (72
+// registers): measured on the 16-view window with 32-splat batches, 20 warps (all state in
+// registers, 96 registers) 3.76 ms, 26 warps 3.58, 28 warps 3.58, 30 and 32 warps (which
+// spill) 4.47 and 4.46 ms.
 constexpr int kFwdMinWarps = 32;
-constexpr int kBwdMinWarps = 20;
+constexpr int kBwdMinWarps = 28;
 template <int B, int P, int MinWarps>
 __host__ __device__ constexpr int min_blocks_for()
 {

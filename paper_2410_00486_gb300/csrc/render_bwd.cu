@@ -24,6 +24,12 @@
 // ten lanes each issue one atomic add into the slot's gradient record; when only a few
 // lanes contributed they add their own sums directly instead.  Warps where no pixel
 // blended the splat skip it (vote).
+//
+// The per-pixel loss gradients (three channels and depth) are constant during the walk and
+// live in shared memory, read once per blended pixel; that leaves 72 registers a thread,
+// so 28 warps stay resident.  With a work counter the grid is persistent: as many blocks
+// as are resident on the GPU take (view, tile) items in the sort's longest-first order
+// from the counter until none is left.
 #include "raster.cuh"
 
 namespace cgs {
@@ -50,13 +56,26 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
     __shared__ float4 s0[BD], s1[BD], s2[BD];
     __shared__ uint32_t sslot[BD];
     __shared__ uint32_t smax[NW];
-    __shared__ __align__(16) float red[NW * 2 * kRedRows * kRedStride];   // per warp, double-buffered
-    int rbuf = 0;
-    for (int i = threadIdx.x; i < NW * 2 * kRedStride; i += NT)   // the zero row of every buffer
+    __shared__ __align__(16) float red[NW * kRedRows * kRedStride];   // per warp
+    __shared__ float4 sgi[PPT * NT];   // per pixel p of thread t at [p NT + t]: dL/dimg (3 channels), dL/ddepth
+    __shared__ uint32_t s_item;
+    for (int i = threadIdx.x; i < NW * kRedStride; i += NT)   // the zero row of every warp's buffer
         red[(i / kRedStride) * (kRedRows * kRedStride) + 32 * kRedStride + i % kRedStride] = 0.f;
+    const uint32_t n_items = (uint32_t)(a.g.Tv * a.V);
+    for (uint32_t it = 0;; it++) {
+    uint32_t item = blockIdx.x;
+    if (a.work) {
+        __syncthreads();   // the previous item's reads of s_item and of the shared state are done
+        if (threadIdx.x == 0) s_item = atomicAdd(a.work, 1u);
+        __syncthreads();
+        item = s_item;
+        if (item >= n_items) break;
+    } else if (it > 0) {
+        break;
+    }
     int64_t tile;
     int view, tx, ty;
-    item_tile(a.order, a.g, tile, view, tx, ty);
+    item_tile(a.order, a.g, tile, view, tx, ty, item);
     const int lane = threadIdx.x & 31;
     const int px = tx * B + (int)(threadIdx.x % B);
     constexpr int G = row_step<B>();
@@ -69,7 +88,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
     // per-pixel state: transmittance, pixel gradients, and S = (colour behind) . gI +
     // (depth behind) gD, where "behind" starts as the background (no depth) and follows
     // R <- alpha c + (1 - alpha) R towards the front
-    float T[PPT], gI0[PPT], gI1[PPT], gI2[PPT], gD[PPT], S[PPT];
+    float T[PPT], S[PPT];
     const float fy0 = (float)py0;   // row of pixel p: fy0 + G p (exact)
     uint32_t lst[PPT];
     uint32_t m = 0;
@@ -78,8 +97,12 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
         const int py = py0 + G * p;
         lst[p] = 0;
         T[p] = 1.f;
-        gI0[p] = gI1[p] = gI2[p] = gD[p] = S[p] = 0.f;
-        if (!(px < a.g.W && py < a.g.H)) continue;
+        S[p] = 0.f;
+        float gI0 = 0.f, gI1 = 0.f, gI2 = 0.f, gD = 0.f;
+        if (!(px < a.g.W && py < a.g.H)) {
+            sgi[p * NT + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
         const size_t q = (size_t)py * a.g.W + px;
         const size_t pix = (size_t)view * HW + q;
         // never walk past the tile's list, whatever `last` holds
@@ -87,25 +110,26 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
         T[p] = a.tfin[pix];
         if (a.dl_dimg) {
             const float *gi = a.dl_dimg + (size_t)view * 3 * HW + q;
-            gI0[p] = gi[0];
-            gI1[p] = gi[HW];
-            gI2[p] = gi[2 * HW];
-            gD[p] = a.dl_ddepth ? a.dl_ddepth[pix] : 0.f;
+            gI0 = gi[0];
+            gI1 = gi[HW];
+            gI2 = gi[2 * HW];
+            gD = a.dl_ddepth ? a.dl_ddepth[pix] : 0.f;
         } else {
             const float w = a.weight ? a.weight[view] : 1.f;
             const float sc = w / (3.f * (float)HW);
             const float *im = a.img + (size_t)view * 3 * HW + q;
             const float *tr = a.tgt_rgb + (size_t)view * 3 * HW + q;
-            gI0[p] = sc * sgnf(im[0] - tr[0]);
-            gI1[p] = sc * sgnf(im[HW] - tr[HW]);
-            gI2[p] = sc * sgnf(im[2 * HW] - tr[2 * HW]);
+            gI0 = sc * sgnf(im[0] - tr[0]);
+            gI1 = sc * sgnf(im[HW] - tr[HW]);
+            gI2 = sc * sgnf(im[2 * HW] - tr[2 * HW]);
             if (a.tgt_depth) {
                 const float td = a.tgt_depth[pix];
                 const int cnt = a.depth_count[view];
-                if (td > 0.f && cnt > 0) gD[p] = w * a.lambda_d * sgnf(a.depth[pix] - td) / (float)cnt;
+                if (td > 0.f && cnt > 0) gD = w * a.lambda_d * sgnf(a.depth[pix] - td) / (float)cnt;
             }
         }
-        S[p] = a.bg0 * gI0[p] + a.bg1 * gI1[p] + a.bg2 * gI2[p];
+        sgi[p * NT + threadIdx.x] = make_float4(gI0, gI1, gI2, gD);
+        S[p] = a.bg0 * gI0 + a.bg1 * gI1 + a.bg2 * gI2;
         m = max(m, lst[p]);
     }
     // block-wide largest `last`: the walk starts there
@@ -163,17 +187,18 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
                 for (int h = 0; h < 2; h++) {
                     const int p = p2 + h;
                     const float dy = dyv[h];
+                    const float4 gi = sgi[p * NT + threadIdx.x];   // dL/dimg, dL/ddepth of pixel p
                     const float G = k[h] ? exp2_fast(pw[h]) : 0.f;
                     const float araw = __fmul_rn(q1.y, G);
                     const float alpha = fminf(kAlphaMax, araw);
                     const float inv_om = rcp_fast(__fsub_rn(1.f, alpha));
                     T[p] = k[h] ? T[p] * inv_om : T[p];               // transmittance before splat j
                     const float wT = alpha * T[p];
-                    gr = fmaf(wT, gI0[p], gr);
-                    gg = fmaf(wT, gI1[p], gg);
-                    gb = fmaf(wT, gI2[p], gb);
-                    gz = fmaf(wT, gD[p], gz);
-                    const float cg = fmaf(q1.z, gD[p], fmaf(q2.z, gI2[p], fmaf(q2.y, gI1[p], q2.x * gI0[p])));
+                    gr = fmaf(wT, gi.x, gr);
+                    gg = fmaf(wT, gi.y, gg);
+                    gb = fmaf(wT, gi.z, gb);
+                    gz = fmaf(wT, gi.w, gz);
+                    const float cg = fmaf(q1.z, gi.w, fmaf(q2.z, gi.z, fmaf(q2.y, gi.y, q2.x * gi.x)));
                     const float diff = cg - S[p];
                     S[p] = fmaf(alpha, diff, S[p]);
                     // dalpha/dpower = alpha, dalpha/dopacity = G, both 0 where alpha is clamped
@@ -213,8 +238,8 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
                 // row, then lanes 10g + f (g < 3, f < 10) add field f over rows g, g + 3,
                 // g + 6, ... and three shuffles combine the groups (row stride 12 floats:
                 // the 16-byte stores are conflict-free, the column reads nearly so)
-                float *buf = red + (size_t)((threadIdx.x >> 5) * 2 + rbuf) * (kRedRows * kRedStride);
-                rbuf ^= 1;
+                float *buf = red + (size_t)(threadIdx.x >> 5) * (kRedRows * kRedStride);
+                __syncwarp();   // the previous sum's column reads are done before the rows are rewritten
                 float4 *row = reinterpret_cast<float4 *>(buf + lane * kRedStride);
                 row[0] = make_float4(m0, sdpy, m0 * dx, m3);
                 row[1] = make_float4(sdpyy, go, gz, gr);
@@ -248,13 +273,33 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
             }
         }
     }
+    }   // work items
 }
 
 template <int B, int BD>
 static cudaError_t launch_bwd(const RasterBwdArgs &a, cudaStream_t s)
 {
-    const int64_t items = a.g.Tv * a.V;
-    k_render_bwd<B, BD><<<(unsigned)items, B * B / ppt_for<B, kPPTBwd>(), 0, s>>>(a);
+    const int nt = B * B / ppt_for<B, kPPTBwd>();
+    int64_t blocks = a.g.Tv * a.V;
+    if (a.work) {
+        // persistent: the resident blocks of the whole GPU (queried once per device and shape)
+        static int resident[64] = {0};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!resident[dev]) {
+            int per_sm = 0, sms = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<B, BD>, nt, 0);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            resident[dev] = max(1, per_sm) * max(1, sms);
+        }
+        blocks = min(blocks, (int64_t)resident[dev]);
+        e = cudaMemsetAsync(a.work, 0, sizeof(uint32_t), s);
+        if (e != cudaSuccess) return e;
+    }
+    if (blocks > 0) k_render_bwd<B, BD><<<(unsigned)blocks, nt, 0, s>>>(a);
     return cudaGetLastError();
 }
 

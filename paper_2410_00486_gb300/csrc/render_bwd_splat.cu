@@ -79,7 +79,7 @@ k_render_bwd_splat(RasterBwdArgs a, const float4 *__restrict__ ck4, const float 
     __shared__ uint32_t smax[kSplatWarps];
     int64_t tile;
     int view, tx, ty;
-    item_tile(a.order, a.g, tile, view, tx, ty);
+    item_tile(a.order, a.g, tile, view, tx, ty, blockIdx.x);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t start = a.ranges[2 * tile];
     const uint32_t len = a.ranges[2 * tile + 1] - start;
@@ -358,6 +358,7 @@ int cgs_raster_bwd_splat(const float *rec, const uint32_t *vals, const uint32_t 
     a.dl_dimg = dl_dimg;
     a.dl_ddepth = dl_ddepth;
     a.sgrad = slot_grad;
+    a.work = nullptr;
     const float4 *ck4 = reinterpret_cast<const float4 *>(ckpt);
     const float *ckD = ckpt + 4 * (size_t)max_buckets * cfg->tile * cfg->tile;
     const unsigned items = (unsigned)(g.Tv * V);

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
     __shared__ float red[5][NW];
     int64_t tile;
     int view, tx, ty;
-    item_tile(a.order, a.g, tile, view, tx, ty);
+    item_tile(a.order, a.g, tile, view, tx, ty, blockIdx.x);
     const int px = tx * B + (int)(threadIdx.x % B);
     constexpr int G = row_step<B>();
     const int row0 = thread_row0<B, PPT>();

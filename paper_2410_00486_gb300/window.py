@@ -40,7 +40,7 @@ class MappingWindow:
                  lambda_depth: float = 0.1, bg=(0.0, 0.0, 0.0), near_z: float = 0.2,
                  betas=(0.9, 0.999), eps: float = 1e-15, capacity: int | None = None,
                  densify_stats: bool = True, tile_order: bool = True, backward: str = "pixel",
-                 lambda_ssim: float = 0.0, batch_depth_bwd: int = 0):
+                 lambda_ssim: float = 0.0, batch_depth_bwd: int = 0, persistent_bwd: bool = True):
         if not params.is_cuda or params.dtype != torch.float32:
             raise ValueError("params must be a float32 CUDA tensor")
         dev = params.device
@@ -87,6 +87,8 @@ class MappingWindow:
         self.order = _u32(self.Ttot, dev) if tile_order else None
         self.n_inst = torch.zeros(1, dtype=torch.int64, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        # work counter of the persistent raster backward (None: one block per tile)
+        self.work = _u32(1, dev) if persistent_bwd else None
 
         self.img = torch.zeros(V, 3, H, W, **f32)
         self.depth = torch.zeros(V, H, W, **f32)
@@ -231,7 +233,7 @@ class MappingWindow:
                          self.order, self.view_weight, self.img, self.depth, self.t_final, self.last,
                          self.tgt_rgb, self.tgt_depth, self.depth_count, dl_dimg, dl_ddepth, self.slot_grad,
                          g, False, self.accum if d else None, self.denom if d else None,
-                         self.max_r2d if d else None, self.status)
+                         self.max_r2d if d else None, self.status, work=self.work)
 
     def optimizer_step(self):
         N.cgs_adam(self.params, self.grads, self.m, self.v, self.n, self.sh_degree, self.lr, self.betas[0],
@@ -357,7 +359,7 @@ class MappingWindow:
             N.cgs_render_bwd(self.params, self.n, cam, 1, c, pv["rec"], self.vals, pv["ranges"], pv["order"], w,
                              img, dep, tf, la, tr, td, dc, gi, gd, pv["slot_grad"], self.grads,
                              v > 0 and not adam_every_view, self.accum if d else None,
-                             self.denom if d else None, self.max_r2d if d else None, self.status)
+                             self.denom if d else None, self.max_r2d if d else None, self.status, work=self.work)
             if adam_every_view:
                 self.optimizer_step()
         if not adam_every_view:

@@ -448,18 +448,26 @@ def test_render_fwd_background_and_ragged_tiles():
     assert np.abs(out["img"].cpu().numpy() - fw["img"]).max(1)[ok].max() < PIX_TOL
 
 
-@pytest.mark.parametrize("name,bd", [("cfg1", 64), ("cfg3", 128), ("tiny_sh3_3views", 32),
-                                     ("room_sh3_20k", 64), ("path_sh3_3views", 256), ("room_t32", 64)])
-def test_raster_bwd_matches_oracle(name, bd):
+@pytest.mark.parametrize("name,bd,persistent", [("cfg1", 64, True), ("cfg3", 128, False), ("tiny_sh3_3views", 32, True),
+                                                ("room_sh3_20k", 64, True), ("room_sh3_20k", 32, False),
+                                                ("path_sh3_3views", 256, True), ("room_t32", 64, True),
+                                                ("room_t32", 32, False)])
+def test_raster_bwd_matches_oracle(name, bd, persistent):
+    """The pixel-parallel raster backward, launched persistent (a work counter) or with one
+    block per tile, against the oracle's hand-derived backward."""
     torch = torch_cuda()
     N = native()
     sc, tgt_rgb, tgt_d, pre, rec, ranges, vals, fw = stage_inputs(name)
     out = gpu_forward_from_rec(N, sc, rec, pre, tgt_rgb, tgt_d, bd)
     V, n = sc.views, sc.n
     sg = torch.zeros(V * n * 12, device="cuda")
+    work = torch.full((1,), 12345, dtype=torch.int32, device="cuda") if persistent else None
     N.cgs_raster_bwd(out["rec"], out["vals"], out["ranges"], out["order"], V, out["cfg"], out["w"], out["img"],
-                     out["depth"], out["T"], out["last"], out["tr"], out["td"], out["dcount"], None, None, sg)
+                     out["depth"], out["T"], out["last"], out["tr"], out["td"], out["dcount"], None, None, sg,
+                     work=work)
     torch.cuda.synchronize()
+    if persistent:    # every item was taken once, plus one failed take per block
+        assert int(work.item()) >= sc.views * N.cgs_tiles_per_view(out["cfg"])
     g = sg_from_gpu(sg)
     ref, ref_mag = O.render_bwd(rec, ranges, vals, V, n, sc.width, sc.height, sc.tile, sc.cams, fw["img"],
                                 fw["depth"], tgt_rgb, tgt_d, fw["depth_count"], with_abs=True)
