@@ -6,8 +6,9 @@
 // most-significant-digit first with the tile id as one full-width digit:
 //   1. k_count_agg   : per (4096-slot chunk, tile) instance counts in shared memory; a
 //                      slot is counted in the tiles of its rect its alpha >= 1/255 ellipse
-//                      reaches (reach_box), and a slot with at most 64 rect tiles keeps
-//                      the decisions as a bit mask for step 3
+//                      reaches (reach_box, over the tiles of the ellipse's bounding box),
+//                      and a slot with at most 64 such tiles keeps the decisions as a bit
+//                      mask for step 3
 //   2. k_scan        : exclusive scan -> tile ranges (the digit's bucket offsets)
 //   3. k_scatter_agg : every instance is written once into its tile's bucket as the
 //                      64-bit key (depth bits << 32 | slot), in one reserved run per
@@ -42,20 +43,20 @@ struct BinWs {
     uint32_t *nbig;      // [1]
     uint32_t *big;       // [Ttot]
     uint32_t *bcount;    // [chunks x Ttot]: per (slot chunk, tile) instance counts
-    uint64_t *masks;     // [V n]: per slot, the tiles of its rect that passed the reach test
+    uint4 *slotrec;      // [V n]: per slot, the count pass's reach decisions (SlotBin)
     uint64_t *keys;      // [capacity]
 };
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Sections: counters (one memset), big-tile list, per-chunk counts and per-slot tile
-// masks (shared-memory path only), keys.
+// Sections: counters (one memset), big-tile list, per-chunk counts and per-slot bin
+// records (shared-memory path only), keys.
 static size_t ws_layout(int64_t capacity, int64_t Ttot, int64_t chunk_counts, int64_t slots, BinWs *w, void *base)
 {
     size_t head = align256(sizeof(uint32_t) * (2 * (size_t)Ttot + 2));
     size_t bigb = align256(sizeof(uint32_t) * (size_t)Ttot);
     size_t chb = align256(sizeof(uint32_t) * (size_t)chunk_counts);
-    size_t mkb = chunk_counts > 0 ? align256(sizeof(uint64_t) * (size_t)slots) : 0;
+    size_t mkb = chunk_counts > 0 ? align256(sizeof(uint4) * (size_t)slots) : 0;
     size_t keyb = align256(sizeof(uint64_t) * (size_t)(capacity > 0 ? capacity : 1));
     if (w && base) {
         char *b = static_cast<char *>(base);
@@ -64,7 +65,7 @@ static size_t ws_layout(int64_t capacity, int64_t Ttot, int64_t chunk_counts, in
         w->nbig = w->cursor + Ttot;
         w->big = reinterpret_cast<uint32_t *>(b + head);
         w->bcount = reinterpret_cast<uint32_t *>(b + head + bigb);
-        w->masks = reinterpret_cast<uint64_t *>(b + head + bigb + chb);
+        w->slotrec = reinterpret_cast<uint4 *>(b + head + bigb + chb);
         w->keys = reinterpret_cast<uint64_t *>(b + head + bigb + chb + mkb);
     }
     return head + bigb + chb + mkb + keyb;
@@ -134,120 +135,223 @@ __global__ void k_count(const float4 *__restrict__ rec, int64_t n, int V, Grid g
 // memory: block (c, v) owns slots [c*kChunk, (c+1)*kChunk) of view v, counts its
 // instances per tile in shared memory and touches each global counter once.
 constexpr int kAggThreads = 512;
+// Three resident blocks per SM (at most 42 registers; the count pass needs 49 unbounded):
+// 1.076 -> 1.064 ms for the whole sort on the 16-view window.
+constexpr int kAggMinBlocks = 3;
 
-// Calls f(tile in view, key) for every tile of the rectangles of the visible slots [s0, s1)
-// of a view that the slot can reach (in_tile), row by row, load-balanced over the lanes of
+// The tiles of rect R that the box [u - ex, u + ex] x [v - ey, v + ey] of the splat's
+// alpha >= 1/255 ellipse (reach_prepare) overlaps, widened by one pixel on every side:
+// reach_box's first test (dx <= ex, dy <= ey) fails on every other tile of R.  With |u|,
+// |v|, ex, ey at most 2^20 the float sums below are within a quarter pixel of exact, well
+// inside the margin; beyond that (or with rect lists) the whole rect is kept.
+__device__ __forceinline__ Rect reach_rect(const ReachPre &e, float u, float v, const Rect &R, const Grid &g)
+{
+    if (e.mode == 0) return Rect{R.x0, R.x0, R.y0, R.y0};   // reaches nothing
+    const float lim = 1048576.f;
+    if (e.mode == 1 || !(fabsf(u) <= lim && fabsf(v) <= lim && e.ex <= lim && e.ey <= lim)) return R;
+    const float inv = 1.f / (float)g.B;   // a power of two: exact
+    Rect T;
+    T.x0 = max(R.x0, (int)floorf(__fmul_rn(__fsub_rn(__fsub_rn(u, e.ex), 1.f), inv)));
+    T.x1 = min(R.x1, (int)floorf(__fmul_rn(__fadd_rn(__fadd_rn(u, e.ex), 1.f), inv)) + 1);
+    T.y0 = max(R.y0, (int)floorf(__fmul_rn(__fsub_rn(__fsub_rn(v, e.ey), 1.f), inv)));
+    T.y1 = min(R.y1, (int)floorf(__fmul_rn(__fadd_rn(__fadd_rn(v, e.ey), 1.f), inv)) + 1);
+    if (T.x1 <= T.x0 || T.y1 <= T.y0) return Rect{R.x0, R.x0, R.y0, R.y0};
+    return T;
+}
+
+// Calls f(tile in view, key) for every tile of the rects of the visible slots [s0, s1) of
+// a view that the slot can reach (in_tile), load-balanced pair by pair over the lanes of
 // each warp: a warp takes the next group of 32 slots from the shared counter `next`
-// (groups differ widely in work), forms the prefix sum of their row counts, and hands out
-// rows round-robin; a lane finds the slot owning row j by a 5-step binary search over the
-// prefix (shuffles).
-// Tile masks: a slot whose rect has at most 64 tiles keeps one bit per tile (row-major over
-// the rect) saying whether it passed the reach test.  The count pass (RECORD) sets them
-// (wm: this warp's 32 shared words) and stores them per slot; the scatter pass (!RECORD)
-// reads them back instead of testing again, and tests only the slots with larger rects.
+// (groups differ widely in work), stages their data in shared memory, forms the prefix
+// sum of their item counts, and hands out one item per lane and step; a lane finds the
+// slot owning item j by a 5-step binary search over the prefix (shuffles) and reads the
+// slot from the stage.  An item is one tile of the slot's reach rect (reach_rect,
+// row-major) to test, or, in the scatter pass for a slot with a recorded mask, one set
+// bit of the mask.
+// Slot bin records (SlotBin, 16 bytes per slot, written by the count pass for every slot
+// of the chunk): a slot whose reach rect has at most 64 tiles keeps one bit per tile
+// (row-major over that rect) saying whether it passed the reach test, with its depth bits
+// and the rect's first tile and width, so the scatter pass emits its tiles from the record
+// alone; a larger rect is marked for testing again; a slot that reaches no tile is zero.
 constexpr int kMaskTiles = 64;
+// SlotBin = (mask low, mask high, depth bits, meta); meta is 0 (no tile), kBinLarge, or
+// kBinSmall | (width - 1) << 15 | first tile (tile id in the view, < 2^15).
+constexpr uint32_t kBinSmall = 0x80000000u, kBinLarge = 0x40000000u;
+static_assert(kAggMaxSmem / sizeof(uint32_t) <= 32768, "first tile of a SlotBin takes 15 bits");
+
+struct PairStage {      // one warp's 32 slots
+    float4 a[32];       // u, v, 1/w (reach rect width w), depth bits
+    int4 b[32];         // reach rect's first tile (id in the view), w, mask kept, x0 | y0 << 16
+    float4 c[32];       // reach test: A, 2B, C, t2
+    float4 d[32];       //             ex, ey, B/C, B/A
+    int4 e[32];         //             mode; tile mask low and high words
+};
+
+// Position of the k-th (from 0) set bit of x; x has more than k set bits.
+__device__ __forceinline__ int nth_bit32(uint32_t x, int k)
+{
+    int pos = 0;
+#pragma unroll
+    for (int h = 16; h > 0; h >>= 1) {
+        const uint32_t lo = x & ((1u << h) - 1u);
+        const int c = __popc(lo);
+        if (k >= c) {
+            k -= c;
+            x >>= h;
+            pos += h;
+        } else {
+            x = lo;
+        }
+    }
+    return pos;
+}
+__device__ __forceinline__ int nth_bit64(uint64_t x, int k)
+{
+    const uint32_t lo = (uint32_t)x;
+    const int c = __popc(lo);
+    return k < c ? nth_bit32(lo, k) : 32 + nth_bit32((uint32_t)(x >> 32), k - c);
+}
 
 template <bool RECORD, class F>
-__device__ __forceinline__ void for_each_tile_row(const float4 *__restrict__ rec, int64_t n, int view, int64_t s0,
-                                                  int64_t s1, const Grid &g, uint32_t *next,
-                                                  unsigned long long *wm, uint64_t *__restrict__ masks, F f)
+__device__ __forceinline__ void for_each_tile_pair(const float4 *__restrict__ rec, int64_t n, int view, int64_t s0,
+                                                   int64_t s1, const Grid &g, uint32_t *next, PairStage &st,
+                                                   uint4 *__restrict__ slotrec, F f)
 {
     const int lane = threadIdx.x & 31;
-    // warps take 32-slot groups from a shared counter (groups differ in work)
     for (;;) {
         uint32_t grp = 0;
         if (lane == 0) grp = atomicAdd(next, 1u);
         grp = __shfl_sync(kFull, grp, 0);
         const int64_t wb = s0 + 32 * (int64_t)grp;
-        if (wb >= s1) break;
+        if (wb >= s1) break;   // warp-uniform
         const int64_t gi = wb + lane;
-        int h = 0, x0 = 0, x1 = 0, y0 = 0;
-        uint32_t zb = 0;
-        float u = 0.f, v = 0.f, z;
+        const int64_t slot = (int64_t)view * n + gi;
+        int cnt = 0, t0 = 0, w = 0, small = 0, xy0 = 0;
+        float u = 0.f, v = 0.f;
+        uint32_t zb = 0u;
         ReachPre e{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
-        int r;
-        if (gi < s1 && load_slot(rec, (int64_t)view * n + gi, u, v, z, r)) {
-            const Rect R = tile_rect(u, v, r, g);
-            if (R.x1 > R.x0 && R.y1 > R.y0) {
-                h = R.y1 - R.y0;
-                x0 = R.x0;
-                x1 = R.x1;
-                y0 = R.y0;
-                zb = __float_as_uint(z);
-                e = load_reach(rec, (int64_t)view * n + gi, g);
+        uint64_t mk = 0ull;
+        bool test = RECORD;   // slot's tiles come from the reach test (else from its mask)
+        if (!RECORD && gi < s1) {
+            const uint4 sb = slotrec[slot];
+            if (sb.w & kBinSmall) {
+                mk = ((uint64_t)sb.y << 32) | sb.x;
+                cnt = __popcll(mk);
+                zb = sb.z;
+                w = (int)((sb.w >> 15) & 63u) + 1;
+                t0 = (int)(sb.w & 0x7fffu);
+                small = 1;
+            } else if (sb.w & kBinLarge) {
+                test = true;
             }
         }
-        const bool small = h * (x1 - x0) <= kMaskTiles;
-        unsigned long long mk = 0ull;
-        if (RECORD) {
-            wm[lane] = 0ull;
-            __syncwarp();
-        } else if (gi < s1 && h > 0 && small) {
-            mk = masks[(int64_t)view * n + gi];
+        float z;
+        int r;
+        if (test && gi < s1 && load_slot(rec, slot, u, v, z, r)) {
+            const Rect R = tile_rect(u, v, r, g);
+            if (R.x1 > R.x0 && R.y1 > R.y0) {
+                e = load_reach(rec, slot, g);
+                const Rect T = reach_rect(e, u, v, R, g);
+                w = T.x1 - T.x0;
+                cnt = w * (T.y1 - T.y0);
+                t0 = T.y0 * g.Tx + T.x0;
+                xy0 = T.x0 | (T.y0 << 16);
+                small = RECORD && cnt <= kMaskTiles;
+                zb = __float_as_uint(z);
+            }
         }
-        int incl = h;
+        st.a[lane] = make_float4(u, v, w ? 1.f / (float)w : 0.f, __uint_as_float(zb));
+        st.b[lane] = make_int4(t0, w, small, xy0);
+        st.c[lane] = make_float4(e.A, e.B2, e.C, e.t2);
+        st.d[lane] = make_float4(e.ex, e.ey, e.bc, e.ba);
+        st.e[lane] = make_int4(e.mode, (int)(uint32_t)mk, (int)(uint32_t)(mk >> 32), 0);
+        __syncwarp();
+        int incl = cnt;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const int y = __shfl_up_sync(kFull, incl, off);
             if (lane >= off) incl += y;
         }
         const int total = __shfl_sync(kFull, incl, 31);
-        for (int r0 = 0; r0 < total; r0 += 32) {
+        for (int r0 = 0; r0 < total; r0 += 32) {   // warp-uniform
             const int j = r0 + lane;
             int L = 0;   // owner: the number of lanes whose inclusive prefix is <= j
 #pragma unroll
             for (int b = 16; b > 0; b >>= 1)
                 if (__shfl_sync(kFull, incl, L + b - 1) <= j) L += b;
-            const int oend = __shfl_sync(kFull, incl, L), oh = __shfl_sync(kFull, h, L);
-            const int ox0 = __shfl_sync(kFull, x0, L), ox1 = __shfl_sync(kFull, x1, L);
-            const int oy0 = __shfl_sync(kFull, y0, L);
-            const uint32_t ozb = __shfl_sync(kFull, zb, L);
-            const float ou = __shfl_sync(kFull, u, L), ov = __shfl_sync(kFull, v, L);
-            const bool osmall = __shfl_sync(kFull, small, L);
-            const unsigned long long omk = RECORD ? 0ull : __shfl_sync(kFull, mk, L);
-            const bool test = j < total && (RECORD || !osmall);
-            ReachPre oe{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
-            if (__any_sync(kFull, test))
-                oe = ReachPre{__shfl_sync(kFull, e.A, L),  __shfl_sync(kFull, e.B2, L), __shfl_sync(kFull, e.C, L),
-                              __shfl_sync(kFull, e.t2, L), __shfl_sync(kFull, e.ex, L), __shfl_sync(kFull, e.ey, L),
-                              __shfl_sync(kFull, e.bc, L), __shfl_sync(kFull, e.ba, L), __shfl_sync(kFull, e.mode, L)};
-            if (j < total) {
-                const uint32_t slot = (uint32_t)((int64_t)view * n + wb + L);
-                const uint64_t key = ((uint64_t)ozb << 32) | (uint64_t)slot;
-                const int row = j - (oend - oh), ty = oy0 + row, ow = ox1 - ox0;
-                if (!RECORD && osmall) {
-                    // the count pass's decisions for this row
-                    unsigned long long bits = (omk >> (row * ow)) & (ow >= 64 ? ~0ull : ((1ull << ow) - 1ull));
-                    while (bits) {
-                        const int b = __ffsll((long long)bits) - 1;
-                        bits &= bits - 1ull;
-                        f(ty * g.Tx + ox0 + b, key);
-                    }
+            const int oend = __shfl_sync(kFull, incl, L), ocnt = __shfl_sync(kFull, cnt, L);
+            const int4 ob = st.b[L];
+            const bool live = j < total;
+            const bool from_mask = !RECORD && ob.z;
+            const int k = j - (oend - ocnt);
+            bool pass = false;
+            if (live) {
+                const float4 oa = st.a[L];
+                const int idx = from_mask ? nth_bit64(((uint64_t)(uint32_t)st.e[L].z << 32) | (uint32_t)st.e[L].y, k)
+                                          : k;   // row-major index into the reach rect
+                int row = (int)(((float)idx + 0.5f) * oa.z), col = idx - row * ob.y;
+                if (col < 0) {           // the float quotient is within one of the exact one
+                    row--;
+                    col += ob.y;
+                } else if (col >= ob.y) {
+                    row++;
+                    col -= ob.y;
+                }
+                const int t = ob.x + row * g.Tx + col;
+                if (from_mask) {
+                    pass = true;
                 } else {
-                    unsigned long long rowbits = 0ull;
-                    for (int tx = ox0; tx < ox1; tx++)
-                        if (in_tile(oe, ou, ov, tx, ty, g)) {
-                            f(ty * g.Tx + tx, key);
-                            if (RECORD && osmall) rowbits |= 1ull << (tx - ox0);   // tx - ox0 < 64
-                        }
-                    if (RECORD && osmall && rowbits) atomicOr(&wm[L], rowbits << (row * ow));
+                    const float4 oc = st.c[L], od = st.d[L];
+                    const ReachPre oe{oc.x, oc.y, oc.z, oc.w, od.x, od.y, od.z, od.w, st.e[L].x};
+                    pass = in_tile(oe, oa.x, oa.y, (ob.w & 0xffff) + col, (ob.w >> 16) + row, g);
+                }
+                if (pass) {
+                    const uint32_t oslot = (uint32_t)((int64_t)view * n + wb + L);
+                    f(t, ((uint64_t)__float_as_uint(oa.w) << 32) | (uint64_t)oslot);
                 }
             }
+            if (RECORD) {
+                // this step's decisions for the masked slots: the first lane of each owner's
+                // run of lanes ORs the run's bits into the owner's mask (one writer per owner
+                // and step)
+                const unsigned bal = __ballot_sync(kFull, pass);
+                const int first = max(0, (oend - ocnt) - r0);
+                if (live && ob.z && lane == first) {
+                    const int runlen = min(oend - r0, 32) - first;
+                    const uint32_t bits = (bal >> first) & (runlen >= 32 ? kFull : ((1u << runlen) - 1u));
+                    const uint64_t m = (((uint64_t)(uint32_t)st.e[L].z << 32) | (uint32_t)st.e[L].y) |
+                                       ((uint64_t)bits << k);   // k + runlen <= kMaskTiles
+                    st.e[L].y = (int)(uint32_t)m;
+                    st.e[L].z = (int)(uint32_t)(m >> 32);
+                }
+                __syncwarp();
+            }
         }
-        if (RECORD) {
-            __syncwarp();
-            if (gi < s1 && h > 0 && small) masks[(int64_t)view * n + gi] = wm[lane];
-            __syncwarp();
+        if (RECORD && gi < s1) {
+            uint4 sb = make_uint4(0u, 0u, 0u, 0u);
+            if (cnt > 0 && small)
+                sb = make_uint4((uint32_t)st.e[lane].y, (uint32_t)st.e[lane].z, zb,
+                                kBinSmall | ((uint32_t)(w - 1) << 15) | (uint32_t)t0);
+            else if (cnt > 0)
+                sb = make_uint4(0u, 0u, zb, kBinLarge);
+            slotrec[slot] = sb;
         }
+        __syncwarp();   // the stage is rewritten by the next group
     }
 }
 
-__global__ void __launch_bounds__(kAggThreads)
+// Dynamic shared memory of the aggregated count and scatter kernels: one PairStage per
+// warp, then the view's tile histogram.
+constexpr int kAggWarps = kAggThreads / 32;
+constexpr size_t kStageBytes = sizeof(PairStage) * kAggWarps;
+
+__global__ void __launch_bounds__(kAggThreads, kAggMinBlocks)
 k_count_agg(const float4 *__restrict__ rec, int64_t n, Grid g, uint32_t *__restrict__ count,
-            uint32_t *__restrict__ bcount, uint64_t *__restrict__ masks)
+            uint32_t *__restrict__ bcount, uint4 *__restrict__ slotrec)
 {
-    __shared__ unsigned long long wmask[kAggThreads / 32][32];
-    extern __shared__ uint32_t hist[];
+    extern __shared__ float4 smem_agg[];
+    PairStage *stage = reinterpret_cast<PairStage *>(smem_agg);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(smem_agg) + kStageBytes);
     const int view = blockIdx.y;
     const int64_t s0 = (int64_t)blockIdx.x * kChunk;
     const int64_t s1 = min(n, s0 + kChunk);
@@ -255,8 +359,8 @@ k_count_agg(const float4 *__restrict__ rec, int64_t n, Grid g, uint32_t *__restr
     for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) hist[t] = 0;
     if (threadIdx.x == 0) next = 0;
     __syncthreads();
-    for_each_tile_row<true>(rec, n, view, s0, s1, g, &next, wmask[threadIdx.x >> 5], masks,
-                            [&](int t, uint64_t) { atomicAdd(&hist[t], 1u); });
+    for_each_tile_pair<true>(rec, n, view, s0, s1, g, &next, stage[threadIdx.x >> 5], slotrec,
+                             [&](int t, uint64_t) { atomicAdd(&hist[t], 1u); });
     __syncthreads();
     uint32_t *base = count + (int64_t)view * g.Tv;
     uint32_t *mine = bcount + ((int64_t)view * gridDim.x + blockIdx.x) * g.Tv;
@@ -346,12 +450,14 @@ __global__ void k_scatter(const float4 *__restrict__ rec, int64_t n, int V, Grid
 // Aggregated scatter (same block decomposition as k_count_agg): the block counts its
 // instances per tile again, reserves one contiguous run per tile in each bucket with a
 // single global atomic, then places its instances with shared-memory atomics.
-__global__ void __launch_bounds__(kAggThreads)
+__global__ void __launch_bounds__(kAggThreads, kAggMinBlocks)
 k_scatter_agg(const float4 *__restrict__ rec, int64_t n, Grid g, const uint32_t *__restrict__ start,
-              uint32_t *__restrict__ cursor, const uint32_t *__restrict__ bcount, uint64_t *__restrict__ masks,
+              uint32_t *__restrict__ cursor, const uint32_t *__restrict__ bcount, uint4 *__restrict__ slotrec,
               uint64_t *__restrict__ keys, int64_t capacity)
 {
-    extern __shared__ uint32_t hist[];     // [Tv] counts, then run positions
+    extern __shared__ float4 smem_agg[];
+    PairStage *stage = reinterpret_cast<PairStage *>(smem_agg);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(smem_agg) + kStageBytes);  // run positions
     const int view = blockIdx.y;
     const int64_t s0 = (int64_t)blockIdx.x * kChunk;
     const int64_t s1 = min(n, s0 + kChunk);
@@ -365,10 +471,11 @@ k_scatter_agg(const float4 *__restrict__ rec, int64_t n, Grid g, const uint32_t 
         hist[t] = c ? start[tbase + t] + atomicAdd(cursor + tbase + t, c) : 0u;
     }
     __syncthreads();
-    for_each_tile_row<false>(rec, n, view, s0, s1, g, &next, nullptr, masks, [&](int t, uint64_t key) {
-        const uint64_t pos = atomicAdd(&hist[t], 1u);
-        if (pos < (uint64_t)capacity) keys[pos] = key;
-    });
+    for_each_tile_pair<false>(rec, n, view, s0, s1, g, &next, stage[threadIdx.x >> 5], slotrec,
+                              [&](int t, uint64_t key) {
+                                  const uint64_t pos = atomicAdd(&hist[t], 1u);
+                                  if (pos < (uint64_t)capacity) keys[pos] = key;
+                              });
 }
 
 // Compare-exchange network of an ascending bitonic sort in which every comparator
@@ -685,22 +792,23 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
     const int64_t slots = (int64_t)V * n;
     const size_t hist_bytes = sizeof(uint32_t) * (size_t)g.Tv;
     const bool agg = hist_bytes <= kAggMaxSmem;
+    const size_t agg_smem = kStageBytes + hist_bytes;
     if (agg) {
-        e = cudaFuncSetAttribute(k_count_agg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hist_bytes);
+        e = cudaFuncSetAttribute(k_count_agg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)agg_smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_scatter_agg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hist_bytes);
+            e = cudaFuncSetAttribute(k_scatter_agg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)agg_smem);
         if (e != cudaSuccess) return e;
     }
     const dim3 agrid((unsigned)((n + kChunk - 1) / kChunk), (unsigned)V);
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((slots + threads - 1) / threads, (int64_t)num_sms * 16);
     if (agg)
-        k_count_agg<<<agrid, kAggThreads, hist_bytes, s>>>(r4, n, g, w.count, w.bcount, w.masks);
+        k_count_agg<<<agrid, kAggThreads, agg_smem, s>>>(r4, n, g, w.count, w.bcount, w.slotrec);
     else
         k_count<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count);
     k_scan<<<1, 1024, 0, s>>>(w.count, Ttot, capacity, ranges, n_inst, status);
     if (agg)
-        k_scatter_agg<<<agrid, kAggThreads, hist_bytes, s>>>(r4, n, g, w.count, w.cursor, w.bcount, w.masks,
+        k_scatter_agg<<<agrid, kAggThreads, agg_smem, s>>>(r4, n, g, w.count, w.cursor, w.bcount, w.slotrec,
                                                              w.keys, capacity);
     else
         k_scatter<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count, w.cursor, w.keys, capacity);

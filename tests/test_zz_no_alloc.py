@@ -54,9 +54,13 @@ def test_noalloc_forward_matches_workspace_forward_twice():
         ws = torch.empty(N.cgs_render_fwd_workspace(V, cfg), dtype=torch.uint8, device="cuda")
         N.cgs_render_fwd(rec, vals, ranges, order, V, cfg, w, tr, td, ref["img"], ref["depth"], ref["T"],
                          ref["last"], ref["loss"], ref["dcount"], ws, status)
+        torch.cuda.synchronize()
+        free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
         N.cgs_render_fwd_noalloc(rec, vals, ranges, order, V, cfg, w, tr, td, got["img"], got["depth"],
                                  got["T"], got["last"], got["loss"], got["dcount"], status)
         torch.cuda.synchronize()
+        if k > 0:   # after the first call's one-time set-up, a call allocates no device memory
+            assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == alloc0
         assert int(status.item()) == 0
         for key in ("img", "depth", "T"):
             assert (got[key] - ref[key]).abs().max().item() <= PIX_TOL, key
