@@ -153,20 +153,16 @@ __device__ __forceinline__ bool reach_box(const ReachPre &p, float u, float v, f
     const float dy = fabsf(__fsub_rn(v, fminf(fmaxf(v, by0), by1)));
     if (!(dx <= p.ex && dy <= p.ey)) return false;
     if (dx == 0.f && dy == 0.f) return true;
-    float qmin = __int_as_float(0x7f800000);   // +infinity
-#pragma unroll
-    for (int e = 0; e < 2; e++) {
-        const float ddx = __fsub_rn(u, e ? bx1 : bx0);
-        const float ddy = fminf(fmaxf(-__fmul_rn(p.bc, ddx), __fsub_rn(v, by1)), __fsub_rn(v, by0));
-        qmin = fminf(qmin, edge_q(p.A, p.B2, p.C, ddx, ddy));
-    }
-#pragma unroll
-    for (int e = 0; e < 2; e++) {
-        const float ddy = __fsub_rn(v, e ? by1 : by0);
-        const float ddx = fminf(fmaxf(-__fmul_rn(p.ba, ddy), __fsub_rn(u, bx1)), __fsub_rn(u, bx0));
-        qmin = fminf(qmin, edge_q(p.A, p.B2, p.C, ddx, ddy));
-    }
-    return qmin <= p.t2;
+    // q is convex with its minimum at the centre, outside the box: its minimum over the box
+    // lies on an edge facing the centre, the vertical edge at the clamped x or the
+    // horizontal edge at the clamped y (where the centre is inside the box's x (y) range,
+    // that "edge" evaluation gives q at a point of the box, which is no lower than the
+    // minimum)
+    const float ddx0 = __fsub_rn(u, fminf(fmaxf(u, bx0), bx1));
+    const float ddy0 = fminf(fmaxf(-__fmul_rn(p.bc, ddx0), __fsub_rn(v, by1)), __fsub_rn(v, by0));
+    const float ddy1 = __fsub_rn(v, fminf(fmaxf(v, by0), by1));
+    const float ddx1 = fminf(fmaxf(-__fmul_rn(p.ba, ddy1), __fsub_rn(u, bx1)), __fsub_rn(u, bx0));
+    return fminf(edge_q(p.A, p.B2, p.C, ddx0, ddy0), edge_q(p.A, p.B2, p.C, ddx1, ddy1)) <= p.t2;
 }
 
 constexpr float kAlphaMax = 0.99f;
