@@ -432,8 +432,9 @@ def main():
     st = win.read_status()
     if st[0] != 0:
         raise SystemExit(f"device status after timing: {st}")
-    # preprocess, count, scan, scatter, sort x2, order, fwd, loss reduce, raster bwd, preprocess bwd, adam,
-    # step counter (the launch list of the captured iteration shows these 13 kernels per step)
+    # preprocess, count, scan x2 (with the work order), scatter, sort x2, fwd, loss reduce, raster bwd,
+    # preprocess bwd, adam, step counter (the launch list of the captured iteration shows these 13 kernels
+    # per step)
     launches_per_step = 13
     gpu_launches = args.steps * launches_per_step
     clocks = clk.summary()

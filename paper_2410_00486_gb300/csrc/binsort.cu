@@ -9,7 +9,8 @@
 //                      reaches (reach_box, over the tiles of the ellipse's bounding box),
 //                      and a slot with at most 64 such tiles keeps the decisions as a bit
 //                      mask for step 3
-//   2. k_scan        : exclusive scan -> tile ranges (the digit's bucket offsets)
+//   2. k_scan_part,  : exclusive scan -> tile ranges (the digit's bucket offsets), and
+//      k_scan_out      the raster work order (tiles by decreasing list length)
 //   3. k_scatter_agg : every instance is written once into its tile's bucket as the
 //                      64-bit key (depth bits << 32 | slot), in one reserved run per
 //                      (chunk, tile); the order inside a bucket is arbitrary
@@ -37,11 +38,17 @@ constexpr size_t kAggMaxSmem = 96 * 1024;   // per-view tile histogram in shared
 // 16-view window but 9% slower for one view at a time (half the blocks).
 constexpr int kChunk = 4096;
 
+// Scan of the per-tile counts: blocks of kScanThreads threads, kScanPer entries each.
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanSpan = kScanThreads * kScanPer;
+constexpr int kLenBuckets = 33;   // list-length buckets of the work order: 0 (empty), 1 + floor(log2 len)
+
 struct BinWs {
     uint32_t *count;     // [Ttot + 1]
     uint32_t *cursor;    // [Ttot]
     uint32_t *nbig;      // [1]
     uint32_t *big;       // [Ttot]
+    unsigned long long *part;   // [scan blocks]: instance total of each scan block
+    uint32_t *bhist;     // [scan blocks x kLenBuckets]: list-length bucket histogram per scan block
     uint32_t *bcount;    // [chunks x Ttot]: per (slot chunk, tile) instance counts
     uint4 *slotrec;      // [V n]: per slot, the count pass's reach decisions (SlotBin)
     uint64_t *keys;      // [capacity]
@@ -55,6 +62,8 @@ static size_t ws_layout(int64_t capacity, int64_t Ttot, int64_t chunk_counts, in
 {
     size_t head = align256(sizeof(uint32_t) * (2 * (size_t)Ttot + 2));
     size_t bigb = align256(sizeof(uint32_t) * (size_t)Ttot);
+    const size_t nsb = (size_t)((Ttot + kScanSpan - 1) / kScanSpan);
+    size_t scb = align256(sizeof(unsigned long long) * nsb) + align256(sizeof(uint32_t) * kLenBuckets * nsb);
     size_t chb = align256(sizeof(uint32_t) * (size_t)chunk_counts);
     size_t mkb = chunk_counts > 0 ? align256(sizeof(uint4) * (size_t)slots) : 0;
     size_t keyb = align256(sizeof(uint64_t) * (size_t)(capacity > 0 ? capacity : 1));
@@ -64,11 +73,13 @@ static size_t ws_layout(int64_t capacity, int64_t Ttot, int64_t chunk_counts, in
         w->cursor = w->count + Ttot + 1;
         w->nbig = w->cursor + Ttot;
         w->big = reinterpret_cast<uint32_t *>(b + head);
-        w->bcount = reinterpret_cast<uint32_t *>(b + head + bigb);
-        w->slotrec = reinterpret_cast<uint4 *>(b + head + bigb + chb);
-        w->keys = reinterpret_cast<uint64_t *>(b + head + bigb + chb + mkb);
+        w->part = reinterpret_cast<unsigned long long *>(b + head + bigb);
+        w->bhist = reinterpret_cast<uint32_t *>(b + head + bigb + align256(sizeof(unsigned long long) * nsb));
+        w->bcount = reinterpret_cast<uint32_t *>(b + head + bigb + scb);
+        w->slotrec = reinterpret_cast<uint4 *>(b + head + bigb + scb + chb);
+        w->keys = reinterpret_cast<uint64_t *>(b + head + bigb + scb + chb + mkb);
     }
-    return head + bigb + chb + mkb + keyb;
+    return head + bigb + scb + chb + mkb + keyb;
 }
 
 // Per-(chunk, tile) counts kept between the count and scatter passes when a view's tile
@@ -371,56 +382,129 @@ k_count_agg(const float4 *__restrict__ rec, int64_t n, Grid g, uint32_t *__restr
     }
 }
 
-// Single-block exclusive scan of the per-tile counts; writes ranges (clamped to the
-// capacity), the total instance count and the capacity status.  Each of the 32 warps
-// owns a contiguous chunk and walks it 32 entries at a time (coalesced loads, warp
-// shuffle scans); a first pass forms the chunk totals.
-__device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long x)
+// Multi-block scan of the per-tile counts and the raster work order (tiles by
+// decreasing list length, bucketed by floor(log2(len)), longest bucket first; tile order
+// inside a bucket is arbitrary), in two launches over blocks of kScanSpan tiles.
+// k_scan_part: each block's instance total and its histogram of length buckets.
+__device__ __forceinline__ uint32_t len_bucket(uint32_t len) { return len ? 32 - __clz(len) : 0; }
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_part(const uint32_t *__restrict__ count, int64_t Ttot, unsigned long long *__restrict__ part,
+            uint32_t *__restrict__ bhist)
 {
-    const int lane = threadIdx.x & 31;
+    __shared__ unsigned long long wsum[kScanThreads / 32];
+    __shared__ uint32_t hist[kLenBuckets];
+    if (threadIdx.x < kLenBuckets) hist[threadIdx.x] = 0u;
+    __syncthreads();
+    const int64_t b0 = (int64_t)blockIdx.x * kScanSpan;
+    unsigned long long sum = 0;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const unsigned long long y = __shfl_up_sync(kFull, x, off);
-        if (lane >= off) x += y;
+    for (int k = 0; k < kScanPer; k++) {
+        const int64_t t = b0 + k * kScanThreads + threadIdx.x;
+        if (t < Ttot) {
+            const uint32_t c = count[t];
+            sum += c;
+            atomicAdd(&hist[len_bucket(c)], 1u);
+        }
     }
-    return x;
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFull, sum, off);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tot = 0;
+        for (int i = 0; i < kScanThreads / 32; i++) tot += wsum[i];
+        part[blockIdx.x] = tot;
+    }
+    if (threadIdx.x < kLenBuckets) bhist[(int64_t)blockIdx.x * kLenBuckets + threadIdx.x] = hist[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(1024)
-k_scan(uint32_t *__restrict__ count, int64_t Ttot, int64_t capacity, uint32_t *__restrict__ ranges,
-       int64_t *__restrict__ n_inst, int32_t *__restrict__ status)
+// k_scan_out: each block adds the earlier blocks' totals, scans its counts into bucket
+// starts (written over the counts, for the scatter) and ranges, both clamped to the
+// capacity, and places its tiles in the work order after every longer bucket's tiles and
+// the earlier blocks' tiles of the same bucket.  Block 0 writes the instance total, the
+// capacity status, and clears the long-tile list.
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_out(uint32_t *__restrict__ count, int64_t Ttot, int64_t capacity, const unsigned long long *__restrict__ part,
+           const uint32_t *__restrict__ bhist, int nblocks, uint32_t *__restrict__ ranges,
+           uint32_t *__restrict__ order, int64_t *__restrict__ n_inst, uint32_t *__restrict__ nbig,
+           int32_t *__restrict__ status)
 {
-    __shared__ unsigned long long wtot[32];
+    __shared__ unsigned long long wtot[kScanThreads / 32];
+    __shared__ unsigned long long s_pre;
+    __shared__ uint32_t btot[kLenBuckets], offs[kLenBuckets];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t per = (Ttot + 31) / 32;
-    const int64_t lo = (int64_t)w * per, hi = min(Ttot, lo + per);
-    unsigned long long s = 0;
-    for (int64_t t = lo + lane; t < hi; t += 32) s += count[t];
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
-    if (lane == 0) wtot[w] = s;
-    __syncthreads();
-    unsigned long long run = 0, total = 0;
-    for (int i = 0; i < 32; i++) {
-        run += (i < w) ? wtot[i] : 0ull;
-        total += wtot[i];
-    }
     const unsigned long long cap = (unsigned long long)capacity;
-    for (int64_t base = lo; base < hi; base += 32) {
-        const int64_t t = base + lane;
-        const unsigned long long c = t < hi ? count[t] : 0ull;
-        const unsigned long long incl = warp_incl_scan(c);
-        const unsigned long long st = run + incl - c, en = run + incl;
-        if (t < hi) {
-            count[t] = (uint32_t)min(st, cap);      // bucket start (clamped) for the scatter
+    if (threadIdx.x == 0) {
+        unsigned long long pre = 0, tot = 0;
+        for (int b = 0; b < nblocks; b++) {
+            const unsigned long long x = part[b];
+            pre += b < (int)blockIdx.x ? x : 0ull;
+            tot += x;
+        }
+        s_pre = pre;
+        if (blockIdx.x == 0) {
+            *nbig = 0u;   // the long-tile list of k_sort_tiles starts empty
+            *n_inst = (int64_t)tot;
+            count[Ttot] = (uint32_t)min(tot, cap);
+            if (tot > cap) set_status(status, CGS_ERR_CAPACITY);
+        }
+    }
+    if (order && threadIdx.x < kLenBuckets) {
+        uint32_t all = 0, before = 0;
+        for (int b = 0; b < nblocks; b++) {
+            const uint32_t x = bhist[(int64_t)b * kLenBuckets + threadIdx.x];
+            all += x;
+            before += b < (int)blockIdx.x ? x : 0u;
+        }
+        btot[threadIdx.x] = all;
+        offs[threadIdx.x] = before;
+    }
+    __syncthreads();
+    if (order && threadIdx.x < kLenBuckets) {
+        uint32_t longer = 0;
+        for (int b = threadIdx.x + 1; b < kLenBuckets; b++) longer += btot[b];
+        offs[threadIdx.x] += longer;
+    }
+    const int64_t b0 = (int64_t)blockIdx.x * kScanSpan;
+    uint32_t c[kScanPer];
+#pragma unroll
+    for (int k = 0; k < kScanPer; k++) {
+        const int64_t t = b0 + k * kScanThreads + threadIdx.x;
+        c[k] = t < Ttot ? count[t] : 0u;
+    }
+    unsigned long long run = s_pre;
+#pragma unroll
+    for (int k = 0; k < kScanPer; k++) {   // 1024 entries at a time, in tile order
+        unsigned long long incl = c[k];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) wtot[w] = incl;
+        __syncthreads();
+        unsigned long long wpre = 0, btot_k = 0;
+        for (int i = 0; i < kScanThreads / 32; i++) {
+            const unsigned long long x = wtot[i];
+            wpre += i < w ? x : 0ull;
+            btot_k += x;
+        }
+        const int64_t t = b0 + k * kScanThreads + threadIdx.x;
+        if (t < Ttot) {
+            const unsigned long long st = run + wpre + incl - c[k], en = run + wpre + incl;
+            count[t] = (uint32_t)min(st, cap);
             ranges[2 * t] = (uint32_t)min(st, cap);
             ranges[2 * t + 1] = (uint32_t)min(en, cap);
         }
-        run += __shfl_sync(kFull, incl, 31);
+        run += btot_k;
+        __syncthreads();   // wtot is rewritten by the next round
     }
-    if (threadIdx.x == 0) {
-        *n_inst = (int64_t)total;
-        count[Ttot] = (uint32_t)min(total, cap);
-        if (total > cap) set_status(status, CGS_ERR_CAPACITY);
+    if (order) {
+#pragma unroll
+        for (int k = 0; k < kScanPer; k++) {
+            const int64_t t = b0 + k * kScanThreads + threadIdx.x;
+            if (t < Ttot) order[atomicAdd(&offs[len_bucket(c[k])], 1u)] = (uint32_t)t;
+        }
     }
 }
 
@@ -750,35 +834,6 @@ k_sort_big(const uint32_t *__restrict__ ranges, uint64_t *__restrict__ keys, uin
     }
 }
 
-// Work order for the raster kernels: tiles by decreasing list length (bucketed by
-// floor(log2(len)), longest bucket first; tile order inside a bucket is arbitrary).
-__global__ void __launch_bounds__(1024)
-k_tile_order(const uint32_t *__restrict__ ranges, int64_t Ttot, uint32_t *__restrict__ order)
-{
-    __shared__ uint32_t hist[33], offs[33];
-    if (threadIdx.x < 33) hist[threadIdx.x] = 0;
-    __syncthreads();
-    for (int64_t t = threadIdx.x; t < Ttot; t += blockDim.x) {
-        uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
-        uint32_t b = len ? 32 - __clz(len) : 0;     // 0 for empty, 1..32 otherwise
-        atomicAdd(&hist[b], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int b = 32; b >= 0; b--) {
-            offs[b] = run;
-            run += hist[b];
-        }
-    }
-    __syncthreads();
-    for (int64_t t = threadIdx.x; t < Ttot; t += blockDim.x) {
-        uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
-        uint32_t b = len ? 32 - __clz(len) : 0;
-        order[atomicAdd(&offs[b], 1u)] = (uint32_t)t;
-    }
-}
-
 cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws, int64_t capacity,
                      uint32_t *vals, uint32_t *ranges, uint32_t *order, int64_t *n_inst, int32_t *status,
                      int num_sms, cudaStream_t s)
@@ -806,7 +861,10 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
         k_count_agg<<<agrid, kAggThreads, agg_smem, s>>>(r4, n, g, w.count, w.bcount, w.slotrec);
     else
         k_count<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count);
-    k_scan<<<1, 1024, 0, s>>>(w.count, Ttot, capacity, ranges, n_inst, status);
+    const int nsb = (int)((Ttot + kScanSpan - 1) / kScanSpan);
+    k_scan_part<<<nsb, kScanThreads, 0, s>>>(w.count, Ttot, w.part, w.bhist);
+    k_scan_out<<<nsb, kScanThreads, 0, s>>>(w.count, Ttot, capacity, w.part, w.bhist, nsb, ranges, order, n_inst,
+                                            w.nbig, status);
     if (agg)
         k_scatter_agg<<<agrid, kAggThreads, agg_smem, s>>>(r4, n, g, w.count, w.cursor, w.bcount, w.slotrec,
                                                              w.keys, capacity);
@@ -817,7 +875,6 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
     e = cudaFuncSetAttribute(k_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem);
     if (e != cudaSuccess) return e;
     k_sort_big<<<num_sms, kBigThreads, big_smem, s>>>(ranges, w.keys, vals, w.big, w.nbig);
-    if (order) k_tile_order<<<1, 1024, 0, s>>>(ranges, Ttot, order);
     return cudaGetLastError();
 }
 
