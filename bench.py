@@ -432,10 +432,10 @@ def main():
     st = win.read_status()
     if st[0] != 0:
         raise SystemExit(f"device status after timing: {st}")
-    # preprocess, count, scan x2 (with the work order), scatter, sort x2, fwd, loss reduce, raster bwd,
-    # preprocess bwd, adam, step counter (the launch list of the captured iteration shows these 13 kernels
+    # preprocess, count, scan x2 (with the work order), scatter, sort x3, fwd, loss reduce, raster bwd,
+    # preprocess bwd, adam, step counter (the launch list of the captured iteration shows these 14 kernels
     # per step)
-    launches_per_step = 13
+    launches_per_step = 14
     gpu_launches = args.steps * launches_per_step
     clocks = clk.summary()
     k_forms = max(MIN_FORM_STEPS, args.steps)

@@ -19,8 +19,9 @@
 //                      well-defined order, (depth, slot) ascending, whatever order the
 //                      scatter produced.  Depth is positive, so its IEEE bits order
 //                      like its values.
-// Buckets longer than kSmallCap go to a second kernel with a larger shared-memory
-// buffer; buckets beyond that are sorted in place in global memory by one block.  When a
+// Buckets longer than kSortCapS are listed for a kernel with larger blocks and buffers,
+// those longer than kSmallCap for a bitonic kernel with a larger shared-memory buffer;
+// buckets beyond that are sorted in place in global memory by one block.  When a
 // view's tile histogram does not fit in shared memory, k_count / k_scatter do steps 1
 // and 3 with global atomics.
 #include <algorithm>
@@ -46,7 +47,9 @@ struct BinWs {
     uint32_t *count;     // [Ttot + 1]
     uint32_t *cursor;    // [Ttot]
     uint32_t *nbig;      // [1]
-    uint32_t *big;       // [Ttot]
+    uint32_t *nmid;      // [1]
+    uint32_t *big;       // [Ttot]: tiles for k_sort_big
+    uint32_t *mid;       // [Ttot]: tiles for k_sort_tiles_l
     unsigned long long *part;   // [scan blocks]: instance total of each scan block
     uint32_t *bhist;     // [scan blocks x kLenBuckets]: list-length bucket histogram per scan block
     uint32_t *bcount;    // [chunks x Ttot]: per (slot chunk, tile) instance counts
@@ -60,8 +63,8 @@ static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // records (shared-memory path only), keys.
 static size_t ws_layout(int64_t capacity, int64_t Ttot, int64_t chunk_counts, int64_t slots, BinWs *w, void *base)
 {
-    size_t head = align256(sizeof(uint32_t) * (2 * (size_t)Ttot + 2));
-    size_t bigb = align256(sizeof(uint32_t) * (size_t)Ttot);
+    size_t head = align256(sizeof(uint32_t) * (2 * (size_t)Ttot + 3));
+    size_t bigb = 2 * align256(sizeof(uint32_t) * (size_t)Ttot);
     const size_t nsb = (size_t)((Ttot + kScanSpan - 1) / kScanSpan);
     size_t scb = align256(sizeof(unsigned long long) * nsb) + align256(sizeof(uint32_t) * kLenBuckets * nsb);
     size_t chb = align256(sizeof(uint32_t) * (size_t)chunk_counts);
@@ -72,7 +75,9 @@ static size_t ws_layout(int64_t capacity, int64_t Ttot, int64_t chunk_counts, in
         w->count = reinterpret_cast<uint32_t *>(b);
         w->cursor = w->count + Ttot + 1;
         w->nbig = w->cursor + Ttot;
+        w->nmid = w->nbig + 1;
         w->big = reinterpret_cast<uint32_t *>(b + head);
+        w->mid = reinterpret_cast<uint32_t *>(b + head + bigb / 2);
         w->part = reinterpret_cast<unsigned long long *>(b + head + bigb);
         w->bhist = reinterpret_cast<uint32_t *>(b + head + bigb + align256(sizeof(unsigned long long) * nsb));
         w->bcount = reinterpret_cast<uint32_t *>(b + head + bigb + scb);
@@ -613,9 +618,15 @@ __device__ __forceinline__ uint32_t next_pow2(uint32_t x)
 // (depth, slot) order.  Stability: warp w owns a contiguous segment of the list and
 // walks it 32 keys at a time; a ballot multisplit ranks equal digits within a step, and
 // per-warp digit histograms scanned digit-major give each (digit, warp) its start.
-constexpr int kRsThreads = 256;
-constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kTieRun = 32;   // longest run of equal 16-bit depth prefixes fixed by insertion
+// Lists of at most kSortCapS keys are sorted by blocks of kSortThreadsS threads (most tiles);
+// longer ones, up to kSmallCap, by blocks of kSortThreadsL threads taking them from a list.
+// Per-tile work that every warp repeats (digit histograms, the digit scan, partial 32-key
+// steps) dominated with eight warps on lists of a few hundred keys: on the 16-view window
+// (lists of 65 to 1.6k keys, 93% of keys in lists of 257 to 1024) four warps and a
+// 1024-key cap took the whole sort from 0.986 to 0.863 ms (eight warps with that cap 0.965,
+// two warps with a 512-key cap 0.886).
+constexpr int kSortThreadsS = 128, kSortCapS = 1024, kSortThreadsL = 256;
 
 // Lanes of the warp whose 8-bit digit equals this lane's (restricted to `valid` lanes),
 // from eight ballots, one per digit bit (a ballot-based multisplit: __match_any_sync
@@ -632,7 +643,9 @@ __device__ __forceinline__ unsigned same_digit_lanes(uint32_t d, unsigned valid)
     return peers;
 }
 
-__device__ __forceinline__ uint32_t block_excl_scan256(uint32_t x, uint32_t *wsum)
+// Exclusive scan over the 32 NW threads of a block.
+template <int NW>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *wsum)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t incl = x;
@@ -649,32 +662,34 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t x, uint32_t *wsu
     return pre + incl - x;
 }
 
-__global__ void __launch_bounds__(kRsThreads)
-k_sort_tiles(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-             uint32_t *__restrict__ big, uint32_t *__restrict__ nbig)
+template <int NTH, int CAP>
+struct SortSmem {
+    uint64_t bufA[CAP], bufB[CAP];
+    uint32_t hist[NTH / 32][256];
+    uint16_t lrank[CAP];
+    uint32_t wsum[NTH / 32], wmin[NTH / 32], wmax[NTH / 32];
+    int s_long;   // a run of equal 16-bit prefixes longer than kTieRun
+};
+
+// Stable LSD radix sort of one tile's list (2 <= len <= CAP keys) in shared memory by a
+// block of NTH threads, written to vals as slot ids.
+template <int NTH, int CAP>
+__device__ __forceinline__ void sort_tile(SortSmem<NTH, CAP> &sm, const uint64_t *__restrict__ keys,
+                                          uint32_t *__restrict__ vals, uint32_t st, uint32_t len)
 {
-    __shared__ uint64_t bufA[kSmallCap], bufB[kSmallCap];
-    __shared__ uint32_t hist[kRsWarps][256];
-    __shared__ uint16_t lrank[kSmallCap];
-    __shared__ uint32_t wsum[kRsWarps], wmin[kRsWarps], wmax[kRsWarps];
-    __shared__ int s_long;   // a run of equal 16-bit prefixes longer than kTieRun
-    const int64_t t = blockIdx.x;
-    const uint32_t st = ranges[2 * t], en = ranges[2 * t + 1];
-    const uint32_t len = en - st;
-    if (len == 0) return;
-    if (len > (uint32_t)kSmallCap) {
-        if (threadIdx.x == 0) big[atomicAdd(nbig, 1u)] = (uint32_t)t;
-        return;
-    }
-    if (len == 1) {
-        if (threadIdx.x == 0) vals[st] = (uint32_t)keys[st];
-        return;
-    }
+    constexpr int NW = NTH / 32;
+    constexpr int DPT = 256 / NTH;   // digits per thread in the digit scan
+    static_assert(DPT >= 1 && DPT * NTH == 256, "a block covers the 256 digits evenly");
+    uint64_t *bufA = sm.bufA, *bufB = sm.bufB;
+    uint32_t (*hist)[256] = sm.hist;
+    uint16_t *lrank = sm.lrank;
+    uint32_t *wsum = sm.wsum, *wmin = sm.wmin, *wmax = sm.wmax;
+    int &s_long = sm.s_long;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // load, and find the range of the depth bits over the tile (positive floats: the bits
     // order like the values)
     uint32_t dmin = ~0u, dmax = 0u;
-    for (uint32_t i = threadIdx.x; i < len; i += kRsThreads) {
+    for (uint32_t i = threadIdx.x; i < len; i += NTH) {
         const uint64_t k = keys[st + i];
         bufA[i] = k;
         const uint32_t d = (uint32_t)(k >> 32);
@@ -693,12 +708,12 @@ k_sort_tiles(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ k
     __syncthreads();
     dmin = ~0u;
     dmax = 0u;
-    for (int i = 0; i < kRsWarps; i++) {
+    for (int i = 0; i < NW; i++) {
         dmin = min(dmin, wmin[i]);
         dmax = max(dmax, wmax[i]);
     }
     uint64_t *src = bufA, *dst = bufB;
-    const uint32_t per = (len + kRsWarps - 1) / kRsWarps;
+    const uint32_t per = (len + NW - 1) / NW;
     const uint32_t seg0 = min(len, (uint32_t)w * per), seg1 = min(len, seg0 + per);
     // The digits are taken from the depth bits less the tile's smallest, r = d - dmin.
     // First attempt: radix passes over the 16 highest bits of r's range [lo, hb) (two
@@ -728,20 +743,24 @@ k_sort_tiles(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ k
                 __syncwarp();
             }
             __syncthreads();
-            {   // start of each (digit, warp) run: digit-major exclusive scan
-                const uint32_t dg = threadIdx.x;       // 256 threads = 256 digits
-                uint32_t cnts[kRsWarps], tot = 0u;
+            {   // start of each (digit, warp) run: digit-major exclusive scan (DPT consecutive
+                // digits per thread)
+                uint32_t cnts[DPT][NW], tot = 0u;
 #pragma unroll
-                for (int i = 0; i < kRsWarps; i++) {
-                    cnts[i] = hist[i][dg];
-                    tot += cnts[i];
-                }
-                uint32_t off = block_excl_scan256(tot, wsum);
+                for (int d = 0; d < DPT; d++)
 #pragma unroll
-                for (int i = 0; i < kRsWarps; i++) {
-                    hist[i][dg] = off;
-                    off += cnts[i];
-                }
+                    for (int i = 0; i < NW; i++) {
+                        cnts[d][i] = hist[i][threadIdx.x * DPT + d];
+                        tot += cnts[d][i];
+                    }
+                uint32_t off = block_excl_scan<NW>(tot, wsum);
+#pragma unroll
+                for (int d = 0; d < DPT; d++)
+#pragma unroll
+                    for (int i = 0; i < NW; i++) {
+                        hist[i][threadIdx.x * DPT + d] = off;
+                        off += cnts[d][i];
+                    }
             }
             __syncthreads();
             for (uint32_t e = seg0 + lane; e < seg1; e += 32) {
@@ -758,7 +777,7 @@ k_sort_tiles(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ k
         // insertion sort by the run's first thread (runs are rare and short)
         const bool check = lo > 0;
         auto rkey = [&](uint32_t i) { return ((uint32_t)(src[i] >> 32) - dmin) >> lo; };
-        for (uint32_t i = threadIdx.x; i + 1 < len; i += kRsThreads) {
+        for (uint32_t i = threadIdx.x; i + 1 < len; i += NTH) {
             const uint32_t di = rkey(i);
             const bool starts = (i == 0 || rkey(i - 1) != di) && rkey(i + 1) == di;
             if (!starts) continue;
@@ -781,14 +800,55 @@ k_sort_tiles(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ k
         __syncthreads();
         if (!s_long) break;      // block-uniform
         // a long run: sort the tile again over every bit of the range
-        for (uint32_t i = threadIdx.x; i < len; i += kRsThreads) bufA[i] = keys[st + i];
+        for (uint32_t i = threadIdx.x; i < len; i += NTH) bufA[i] = keys[st + i];
         src = bufA;
         dst = bufB;
         lo = 0;
         __syncthreads();
         if (threadIdx.x == 0) s_long = 0;
     }
-    for (uint32_t i = threadIdx.x; i < len; i += kRsThreads) vals[st + i] = (uint32_t)src[i];
+    for (uint32_t i = threadIdx.x; i < len; i += NTH) vals[st + i] = (uint32_t)src[i];
+}
+
+// Tiles of at most kSortCapS keys; longer ones are listed (mid) for k_sort_tiles_l.
+__global__ void __launch_bounds__(kSortThreadsS)
+k_sort_tiles(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+             uint32_t *__restrict__ mid, uint32_t *__restrict__ nmid)
+{
+    __shared__ SortSmem<kSortThreadsS, kSortCapS> sm;
+    const int64_t t = blockIdx.x;
+    const uint32_t st = ranges[2 * t], en = ranges[2 * t + 1];
+    const uint32_t len = en - st;
+    if (len == 0) return;
+    if (len > (uint32_t)kSortCapS) {
+        if (threadIdx.x == 0) mid[atomicAdd(nmid, 1u)] = (uint32_t)t;
+        return;
+    }
+    if (len == 1) {
+        if (threadIdx.x == 0) vals[st] = (uint32_t)keys[st];
+        return;
+    }
+    sort_tile<kSortThreadsS, kSortCapS>(sm, keys, vals, st, len);
+}
+
+// The listed longer tiles (persistent blocks); those above kSmallCap go to k_sort_big.
+__global__ void __launch_bounds__(kSortThreadsL)
+k_sort_tiles_l(const uint32_t *__restrict__ ranges, const uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+               const uint32_t *__restrict__ mid, const uint32_t *__restrict__ nmid, uint32_t *__restrict__ big,
+               uint32_t *__restrict__ nbig)
+{
+    __shared__ SortSmem<kSortThreadsL, kSmallCap> sm;
+    const uint32_t nm = *nmid;
+    for (uint32_t mi = blockIdx.x; mi < nm; mi += gridDim.x) {   // block-uniform
+        const uint32_t t = mid[mi];
+        const uint32_t st = ranges[2 * t], len = ranges[2 * t + 1] - st;
+        if (len > (uint32_t)kSmallCap) {
+            if (threadIdx.x == 0) big[atomicAdd(nbig, 1u)] = t;
+        } else {
+            sort_tile<kSortThreadsL, kSmallCap>(sm, keys, vals, st, len);
+        }
+        __syncthreads();   // the shared buffers are reused by the next tile
+    }
 }
 
 __global__ void __launch_bounds__(kBigThreads)
@@ -842,7 +902,7 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
     BinWs w{};
     ws_layout(capacity, Ttot, chunk_count_entries(n, V, g.Tv), (int64_t)V * n, &w, ws);
     const float4 *r4 = reinterpret_cast<const float4 *>(rec);
-    cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (2 * (size_t)Ttot + 2), s);
+    cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (2 * (size_t)Ttot + 3), s);
     if (e != cudaSuccess) return e;
     const int64_t slots = (int64_t)V * n;
     const size_t hist_bytes = sizeof(uint32_t) * (size_t)g.Tv;
@@ -870,7 +930,9 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
                                                              w.keys, capacity);
     else
         k_scatter<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count, w.cursor, w.keys, capacity);
-    k_sort_tiles<<<(unsigned)Ttot, kRsThreads, 0, s>>>(ranges, w.keys, vals, w.big, w.nbig);
+    k_sort_tiles<<<(unsigned)Ttot, kSortThreadsS, 0, s>>>(ranges, w.keys, vals, w.mid, w.nmid);
+    k_sort_tiles_l<<<(unsigned)std::min<int64_t>(Ttot, (int64_t)num_sms * 4), kSortThreadsL, 0, s>>>(
+        ranges, w.keys, vals, w.mid, w.nmid, w.big, w.nbig);
     const size_t big_smem = sizeof(uint64_t) * kBigCap;
     e = cudaFuncSetAttribute(k_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem);
     if (e != cudaSuccess) return e;
