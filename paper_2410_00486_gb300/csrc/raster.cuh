@@ -112,16 +112,18 @@ __host__ __device__ constexpr int min_blocks_for()
 // Staged splat, derived from its record with the exponent in base 2 (every term scaled
 // by log2 e, one rounding each), so alpha = opacity 2^power2 takes the hardware's base-2
 // exponential (PTX ex2.approx) and no multiply per pair:
-//   s0 = (u, v, -A/2 L, -B L), s1 = (-C/2 L, opacity, depth, tau L),  L = log2 e,
-// where tau = -ln(255 opacity): alpha = opacity exp(power) < 1/255 exactly when
-// power < tau, so the raster kernels test the base-2 exponent against tau L and evaluate
-// the exponential only for pairs that can blend.
+//   s0 = (u, v, -A/2 L, -B L), s1 = (-C/2 L, opacity, depth, -tau L),  L = log2 e,
+// where tau = -ln(255 opacity) < 0: alpha = opacity exp(power) < 1/255 exactly when
+// power < tau.  The exponent of a positive-definite conic is at most 0, so a pair can
+// blend exactly when |power| <= -tau: one compare per pair (a rounded power a hair above 0,
+// at a pixel within rounding of the splat's centre, counts as 0, where the exact power
+// lies); the exponential is evaluated only for pairs that pass.
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 __device__ __forceinline__ void stage_splat(const float4 &r0, const float4 &r1, float tau, float4 &t0, float4 &t1)
 {
     t0 = make_float4(r0.x, r0.y, __fmul_rn(r0.z, -0.5f * kLog2e), __fmul_rn(r0.w, -kLog2e));
-    t1 = make_float4(__fmul_rn(r1.x, -0.5f * kLog2e), r1.y, r1.z, __fmul_rn(tau, kLog2e));
+    t1 = make_float4(__fmul_rn(r1.x, -0.5f * kLog2e), r1.y, r1.z, __fmul_rn(tau, -kLog2e));
 }
 
 // 1/x (PTX rcp.approx.ftz) for x = 1 - alpha in [0.01, 1].
@@ -132,7 +134,7 @@ __device__ __forceinline__ float rcp_fast(float x)
     return y;
 }
 
-// 2^x (PTX ex2.approx.ftz; x is at least tau L > -9 here, so nothing is flushed).
+// 2^x (PTX ex2.approx.ftz; |x| is at most -tau L < 9 here, so nothing is flushed).
 __device__ __forceinline__ float exp2_fast(float x)
 {
     float y;

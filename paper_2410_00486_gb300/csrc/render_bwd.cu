@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
                     const int p = p2 + h;
                     dyv[h] = __fsub_rn(q0.y, fy0 + (float)(G * p));
                     pw[h] = power_at(pxs, q1.x, dyv[h]);
-                    k[h] = pos < lst[p] && !(pw[h] > 0.f || pw[h] < q1.w);
+                    k[h] = pos < lst[p] && fabsf(pw[h]) <= q1.w;
                 }
                 if (!(k[0] || k[1])) continue;
                 contrib = true;

@@ -186,7 +186,7 @@ k_render_bwd_splat(RasterBwdArgs a, const float4 *__restrict__ ck4, const float 
             const float dx = __fsub_rn(q0.x, (float)(tx * B + p % B));
             const float dy = __fsub_rn(q0.y, (float)(ty * B + p / B));
             const float power = staged_power(q0, q1.x, dx, dy);
-            if (power > 0.f || power < q1.w) continue;
+            if (!(fabsf(power) <= q1.w)) continue;
             const float G = exp2_fast(power);
             const float araw = __fmul_rn(q1.y, G);
             const float alpha = fminf(kAlphaMax, araw);

@@ -4,8 +4,8 @@
 // tile's depth-sorted list (only splats that can reach alpha >= 1/255 in the tile: the
 // binning's test) is consumed in batches of BD splats: the block gathers the records of a
 // batch (48 bytes each, one per thread) into shared memory; every pixel then walks the
-// batch front to back, rejecting a pair on its base-2 exponent (power < tau, both scaled
-// by log2 e) before any exponential.  A block-wide vote (__syncthreads_count) ends the walk
+// batch front to back, rejecting a pair on its base-2 exponent (|power| > -tau, both
+// scaled by log2 e) before any exponential.  A block-wide vote (__syncthreads_count) ends the walk
 // as soon as every pixel of the tile is saturated (T below 1e-4).
 #include "raster.cuh"
 
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTFwd>(), (min_blocks_for<
                 for (int p = 0; p < PPT; p++) {
                     const float power = power_at(pxs, q1.x, __fsub_rn(q0.y, fy[p]));
                     // the alpha >= 1/255 test; a finished pixel (row NaN, so power NaN) fails it
-                    if (!(power <= 0.f && power >= q1.w)) continue;
+                    if (!(fabsf(power) <= q1.w)) continue;
                     const float alpha = fminf(kAlphaMax, __fmul_rn(q1.y, exp2_fast(power)));
                     const float wgt = __fmul_rn(alpha, T[p]);
                     const float testT = __fsub_rn(T[p], wgt);   // T (1 - alpha)
