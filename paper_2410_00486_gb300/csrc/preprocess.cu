@@ -14,7 +14,11 @@ namespace cgs {
 
 constexpr int kGB = 128;         // Gaussians per block (64: backward 0.53 ms, 128: 0.44 on the 16-view window)
 constexpr int kPreThreads = 256;
-constexpr int kPreBwdMinBlocks = 2;   // resident blocks per SM the backward is compiled for
+// Resident blocks per SM the backward is compiled for.  With the covariance staged per
+// Gaussian and its chain to scale and rotation run once per Gaussian, three blocks fit
+// (at most 85 registers, 73 KB of shared memory on 16 views): 0.404 -> 0.382 ms on the
+// 16-view window (two blocks at 124 registers before: 0.415 ms).
+constexpr int kPreBwdMinBlocks = 3;
 constexpr int kViewChunk = 64;        // views per compaction round of the backward
 static_assert(kGB * kViewChunk / kPreThreads <= 32, "a thread's visibility bits of a view chunk fit one word");
 constexpr int kCamF = 23;        // staged camera: 20 ABI floats + camera centre
@@ -109,14 +113,33 @@ __device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, const fl
 // Shared-memory view of one block's parameters.
 struct Staged {
     const float *means, *scales, *quats, *opac, *dc, *rest, *cams;
+    const float *cov;   // 3-D covariance of each Gaussian (view-independent): xx xy xz yy yz zz
 };
+
+// Activations and frame of Gaussian gl: scale s = exp(log_scale), unit quaternion qn =
+// q / |q| (qinv = 1/|q|), its rotation R, and M = R diag(s), so Sigma = M M^T.
+__device__ __forceinline__ void gauss_frame(const Staged &st, int gl, float s[3], float qn[4], float &qinv,
+                                            float R[9], float M[9])
+{
+    for (int i = 0; i < 3; i++) s[i] = expf(st.scales[3 * gl + i]);
+    const float *q = st.quats + 4 * gl;
+    float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    qinv = 1.0f / sqrtf(qq);
+    for (int i = 0; i < 4; i++) qn[i] = q[i] * qinv;
+    const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);     R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);     R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);     R[7] = 2.f * (y * z + w * x);     R[8] = 1.f - 2.f * (x * x + y * y);
+    for (int r = 0; r < 3; r++)
+        for (int j = 0; j < 3; j++) M[3 * r + j] = R[3 * r + j] * s[j];
+}
 
 template <int DEG>
 struct Proj {
     static constexpr int K = (DEG + 1) * (DEG + 1);
     bool visible;
     float t[3], itz;
-    float s[3], qn[4], qinv, R[9], M[9], S[6];  // S: xx xy xz yy yz zz
+    float S[6];  // 3-D covariance (staged): xx xy xz yy yz zz
     bool xcl, ycl;
     float xs, ys, limx, limy;
     float T0[3], T1[3];
@@ -145,25 +168,7 @@ __device__ __forceinline__ void project(const Staged &st, int gl, const float *c
     if (!(o.t[2] > near_z)) return;
     const float fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
 
-    // activations
-    for (int i = 0; i < 3; i++) o.s[i] = expf(st.scales[3 * gl + i]);
-    const float *q = st.quats + 4 * gl;
-    float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-    o.qinv = 1.0f / sqrtf(qq);
-    for (int i = 0; i < 4; i++) o.qn[i] = q[i] * o.qinv;
-    const float w = o.qn[0], x = o.qn[1], y = o.qn[2], z = o.qn[3];
-    o.R[0] = 1.f - 2.f * (y * y + z * z); o.R[1] = 2.f * (x * y - w * z);     o.R[2] = 2.f * (x * z + w * y);
-    o.R[3] = 2.f * (x * y + w * z);     o.R[4] = 1.f - 2.f * (x * x + z * z); o.R[5] = 2.f * (y * z - w * x);
-    o.R[6] = 2.f * (x * z - w * y);     o.R[7] = 2.f * (y * z + w * x);     o.R[8] = 1.f - 2.f * (x * x + y * y);
-    for (int r = 0; r < 3; r++)
-        for (int j = 0; j < 3; j++) o.M[3 * r + j] = o.R[3 * r + j] * o.s[j];
-    // Sigma = M M^T
-    o.S[0] = o.M[0] * o.M[0] + o.M[1] * o.M[1] + o.M[2] * o.M[2];
-    o.S[1] = o.M[0] * o.M[3] + o.M[1] * o.M[4] + o.M[2] * o.M[5];
-    o.S[2] = o.M[0] * o.M[6] + o.M[1] * o.M[7] + o.M[2] * o.M[8];
-    o.S[3] = o.M[3] * o.M[3] + o.M[4] * o.M[4] + o.M[5] * o.M[5];
-    o.S[4] = o.M[3] * o.M[6] + o.M[4] * o.M[7] + o.M[5] * o.M[8];
-    o.S[5] = o.M[6] * o.M[6] + o.M[7] * o.M[7] + o.M[8] * o.M[8];
+    for (int i = 0; i < 6; i++) o.S[i] = st.cov[6 * gl + i];
 
     // perspective Jacobian with the guard band (1.3 x half field of view)
     const float tz = o.t[2];
@@ -262,6 +267,8 @@ __device__ __forceinline__ Staged stage(float *sm, const float *__restrict__ P, 
         *dst[gi] = cur;
         cur += w * kGB;
     }
+    float *cov = cur;   // filled below, once the parameters are staged
+    cur += 6 * kGB;
     // cameras: 20 ABI floats + centre c = -R^T t
     const float *cf = reinterpret_cast<const float *>(cams);
     for (int i = threadIdx.x; i < V * 20; i += blockDim.x) cur[(i / 20) * kCamF + (i % 20)] = __ldg(cf + i);
@@ -271,6 +278,19 @@ __device__ __forceinline__ Staged stage(float *sm, const float *__restrict__ P, 
         for (int i = 0; i < 3; i++) c[20 + i] = -(c[i] * c[9] + c[3 + i] * c[10] + c[6 + i] * c[11]);
     }
     st.cams = cur;
+    st.cov = cov;
+    // Sigma = M M^T of each Gaussian, once for all views
+    for (int gl = threadIdx.x; gl < cnt; gl += blockDim.x) {
+        float sc[3], qn[4], qinv, R[9], M[9];
+        gauss_frame(st, gl, sc, qn, qinv, R, M);
+        float *S = cov + 6 * gl;
+        S[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+        S[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+        S[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+        S[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+        S[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+        S[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+    }
     __syncthreads();
     return st;
 }
@@ -278,7 +298,7 @@ __device__ __forceinline__ Staged stage(float *sm, const float *__restrict__ P, 
 template <int DEG>
 __host__ __device__ constexpr int staged_floats()
 {
-    return kGB * (14 + 3 * ((DEG + 1) * (DEG + 1) - 1));
+    return kGB * (14 + 3 * ((DEG + 1) * (DEG + 1) - 1) + 6);   // parameter groups + covariance
 }
 
 template <int DEG>
@@ -409,19 +429,42 @@ __device__ __forceinline__ void project_bwd(const Staged &st, int gl, const floa
     for (int i = 0; i < 3; i++) dmean[i] += Rc[i] * dt0 + Rc[3 + i] * dt1 + Rc[6 + i] * dt2;
     for (int i = 0; i < 3; i++) atomicAdd(&a_means[3 * gl + i], dmean[i]);
 
-    // Sigma = M M^T, M = R diag(s): dL/dM = 2 GS M
+    // dL/dSigma (symmetric; upper triangle) gathered over the Gaussian's views: the chain to
+    // scale and rotation is linear in it and runs once per Gaussian (sigma_bwd)
+    float *a_cov = acc + (14 + 3 * (K - 1)) * kGB;
+    atomicAdd(&a_cov[6 * gl + 0], GS[0]);
+    atomicAdd(&a_cov[6 * gl + 1], GS[1]);
+    atomicAdd(&a_cov[6 * gl + 2], GS[2]);
+    atomicAdd(&a_cov[6 * gl + 3], GS[4]);
+    atomicAdd(&a_cov[6 * gl + 4], GS[5]);
+    atomicAdd(&a_cov[6 * gl + 5], GS[8]);
+}
+
+// Sigma = M M^T, M = R diag(s), with G = dL/dSigma summed over the views: dL/dM = 2 G M,
+// then dL/ds and dL/dR, and the rotation of the unit quaternion back through its
+// normalisation; written into the scale and quaternion accumulators of Gaussian gl.
+template <int DEG>
+__device__ __forceinline__ void sigma_bwd(const Staged &st, int gl, float *acc)
+{
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    float *a_scales = acc + 3 * kGB;
+    float *a_quats = acc + 6 * kGB;
+    const float *a_cov = acc + (14 + 3 * (K - 1)) * kGB;
+    float sc[3], qn[4], qinv, R[9], M[9];
+    gauss_frame(st, gl, sc, qn, qinv, R, M);
+    const float *g6 = a_cov + 6 * gl;
+    const float GS[9] = {g6[0], g6[1], g6[2], g6[1], g6[3], g6[4], g6[2], g6[4], g6[5]};
     float GR[9];
     for (int j = 0; j < 3; j++) {
         float ds = 0.f;
         for (int r = 0; r < 3; r++) {
-            float gm = 2.f * (GS[3 * r] * o.M[j] + GS[3 * r + 1] * o.M[3 + j] + GS[3 * r + 2] * o.M[6 + j]);
-            ds += gm * o.R[3 * r + j];
-            GR[3 * r + j] = gm * o.s[j];
+            float gm = 2.f * (GS[3 * r] * M[j] + GS[3 * r + 1] * M[3 + j] + GS[3 * r + 2] * M[6 + j]);
+            ds += gm * R[3 * r + j];
+            GR[3 * r + j] = gm * sc[j];
         }
-        atomicAdd(&a_scales[3 * gl + j], ds * o.s[j]);
+        a_scales[3 * gl + j] = ds * sc[j];
     }
-    // rotation matrix of the unit quaternion -> quaternion, then through normalisation
-    const float w = o.qn[0], x = o.qn[1], y = o.qn[2], z = o.qn[3];
+    const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
     float dq0 = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
     float dq1 = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6] +
                        w * GR[7] - 2.f * x * GR[8]);
@@ -430,10 +473,10 @@ __device__ __forceinline__ void project_bwd(const Staged &st, int gl, const floa
     float dq3 = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] + y * GR[5] +
                        x * GR[6] + y * GR[7]);
     float pr = dq0 * w + dq1 * x + dq2 * y + dq3 * z;
-    atomicAdd(&a_quats[4 * gl + 0], (dq0 - w * pr) * o.qinv);
-    atomicAdd(&a_quats[4 * gl + 1], (dq1 - x * pr) * o.qinv);
-    atomicAdd(&a_quats[4 * gl + 2], (dq2 - y * pr) * o.qinv);
-    atomicAdd(&a_quats[4 * gl + 3], (dq3 - z * pr) * o.qinv);
+    a_quats[4 * gl + 0] = (dq0 - w * pr) * qinv;
+    a_quats[4 * gl + 1] = (dq1 - x * pr) * qinv;
+    a_quats[4 * gl + 2] = (dq2 - y * pr) * qinv;
+    a_quats[4 * gl + 3] = (dq3 - z * pr) * qinv;
 }
 
 template <int DEG>
@@ -509,6 +552,8 @@ k_preprocess_bwd(const float *__restrict__ P, int64_t n, const cgs_camera *__res
         }
         __syncthreads();   // the item list is rebuilt for the next chunk of views
     }
+    for (int gl = threadIdx.x; gl < cnt; gl += blockDim.x) sigma_bwd<DEG>(st, gl, acc);
+    __syncthreads();
     // write the block's slice of every group (coalesced)
     const Layout L = param_layout(n, DEG);
     const int widths[6] = {3, 3, 4, 1, 3, 3 * (K - 1)};
@@ -556,7 +601,7 @@ static cudaError_t launch_pre_bwd(const float *P, int64_t n, const cgs_camera *c
                                   int accumulate, float *accum, float *denom, float *maxr, cudaStream_t s)
 {
     size_t smem = sizeof(float) * (2 * (size_t)staged_floats<DEG>() + 3 * kGB + (size_t)V * kCamF) +
-                  sizeof(uint16_t) * (size_t)kGB * kViewChunk;
+                  sizeof(uint16_t) * (size_t)kGB * min(V, kViewChunk);
     auto k = k_preprocess_bwd<DEG>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
