@@ -110,10 +110,10 @@ int64_t cgs_tiles_per_view(const cgs_config *cfg);
  * V views.
  *   params    device, parameter vector (layout above), n Gaussians
  *   cams      device, cgs_camera[V]
- *   rec       device out, float[V*n][12] records (every slot's radius is written;
- *             other fields only for visible slots)
- *   slot_grad device out, float[V*n][12]; zeroed for every visible slot so the
- *             backward can accumulate into it (may be NULL to skip)
+ *   rec       device out, float[V*n][12] records (every slot's record is written; a
+ *             culled slot's is all zero, radius 0)
+ *   slot_grad device out, float[V*n][12]; zeroed for every slot so the backward
+ *             can accumulate into it (may be NULL to skip)
  * Errors: CGS_ERR_ARG for null/unaligned pointers, n < 1, V < 1, V*n >= 2^32,
  * unsupported tile / sh_degree / sizes.
  */

@@ -318,7 +318,19 @@ k_preprocess(const float *__restrict__ P, int64_t n, const cgs_camera *__restric
         project<DEG>(st, gl, st.cams + v * kCamF, grid, near_z, o);
         float4 *r = rec + kRec4 * slot;
         if (!o.visible) {
-            reinterpret_cast<float *>(r)[7] = __int_as_float(0);
+            // the whole record (radius 0 marks it culled) and slot gradient: with only the
+            // radius word written, DRAM read back and rewrote each partly written sector (0.185
+            // -> 0.165 ms on the 16-view window)
+            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+            r[0] = zero;
+            r[1] = zero;
+            r[2] = zero;
+            if (sgrad) {
+                float4 *gp = sgrad + kRec4 * slot;
+                gp[0] = zero;
+                gp[1] = zero;
+                gp[2] = zero;
+            }
             continue;
         }
         r[0] = make_float4(o.u, o.v, o.A, o.B);
