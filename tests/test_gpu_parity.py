@@ -115,13 +115,17 @@ def gpu_bin(N, rec_gpu, n, V, cfg, capacity, order=True):
 
 
 BIN_CASES = [
-    # V, n, W, H, B, max radius
-    (1, 500, 160, 120, 16, 30),
+    # V, n, W, H, B, max radius; rect-list lengths in the comments decide the sort path
+    (1, 500, 160, 120, 16, 30),      # lists of 8-24
     (3, 2000, 200, 150, 8, 20),
     (2, 3000, 321, 247, 32, 60),
-    (1, 6000, 64, 48, 16, 10),       # lists of 1k-2k: the block-per-tile kernel
-    (1, 12000, 64, 48, 16, 10),      # lists of 2k-16k: the large-bucket kernel
-    (1, 40000, 32, 32, 16, 6),       # lists > 16k: the in-place global sort
+    (1, 6000, 64, 48, 16, 10),       # lists of 362-397: four-warp blocks
+    (1, 12000, 64, 48, 16, 10),      # lists of 710-808
+    (1, 16000, 64, 48, 16, 10),      # lists of 948-1043: four-warp blocks and the long-list kernel
+    (1, 20000, 64, 48, 16, 10),      # lists of 1242-1342: the long-list kernel (eight warps)
+    (1, 30000, 64, 48, 16, 10),      # lists of 1805-2002: the long-list kernel near its 2048 cap
+    (1, 40000, 32, 32, 16, 6),       # lists of 5381-5437: the large-bucket kernel (shared-memory bitonic)
+    (1, 70000, 16, 16, 16, 6),       # one list of 18275 > 16k: the in-place global sort
     (1, 3000, 640, 480, 8, 120),     # rects far above 64 tiles: the scatter repeats the reach test
     (2, 1500, 333, 250, 16, 90),     # mixed rect sizes around the 64-tile mask limit, ragged edges
 ]
@@ -233,15 +237,17 @@ def test_bin_sort_thin_ellipses_at_the_rect_edge():
             print(f"[bin thin ellipses] rect {tot} kept {kept} dropped {dropped}")
 
 
-def test_bin_sort_depth_ties_bit_exact():
+@pytest.mark.parametrize("extra", [0, 1200])
+def test_bin_sort_depth_ties_bit_exact(extra):
     """Depths the per-tile sort's first attempt cannot tell apart (it orders by the 16
     highest bits of depth less the tile's smallest, over the tile's range): a run of 100
     (the tile is sorted again over every bit), runs of two one ulp apart, exact duplicates
-    (slot order); a near and a far splat over every tile make the range wide."""
+    (slot order); a near and a far splat over every tile make the range wide.  With `extra`
+    small splats inside tile 0 its list passes 1024 keys and goes to the long-list kernel."""
     torch = torch_cuda()
     N = native()
     rng = np.random.default_rng(41)
-    W, H, B, n = 64, 48, 16, 1000
+    W, H, B, n = 64, 48, 16, 1000 + extra
     u = rng.uniform(0, W, n)
     v = rng.uniform(0, H, n)
     r = rng.integers(1, 9, n).astype(np.int32)
@@ -256,6 +262,8 @@ def test_bin_sort_depth_ties_bit_exact():
     u[102:162], v[102:162], r[102:162], z[102:162] = rng.uniform(36, 44, 60), rng.uniform(20, 28, 60), 4, pair
     u[162:172], v[162:172], r[162:172] = rng.uniform(52, 60, 10), rng.uniform(36, 44, 10), 4
     z[162:172] = np.repeat(rng.uniform(2.0, 30.0, 5).astype(np.float32), 2)
+    if extra:
+        u[1000:], v[1000:], r[1000:] = rng.uniform(4, 12, extra), rng.uniform(4, 12, extra), 2
     conic = np.zeros((n, 3), np.float32)
     conic[:, 0] = conic[:, 2] = (3.0 / r.astype(np.float32)) ** 2
     opac = np.full(n, 0.9)
@@ -266,7 +274,8 @@ def test_bin_sort_depth_ties_bit_exact():
     ranges_o, vals_o = O.bin_lists(u, v, z.astype(np.float64), r, 1, n, W, H, B)
     cnt = len(vals_o)
     lens = ranges_o[:, 1].astype(np.int64) - ranges_o[:, 0]
-    assert lens.max() < 2048 and lens[0] > 100     # the block-per-tile kernel; tile 0 holds the run of 100
+    assert lens.max() < 2048 and lens[0] > 100     # tile 0 holds the run of 100
+    assert (lens[0] > 1024) == (extra > 0)           # four-warp blocks, or the long-list kernel
     for rect in (True, False):
         cfg = N.make_config(W, H, B, 64, 0, rect_lists=rect)
         vals, ranges, _, ninst, st = gpu_bin(N, g, n, 1, cfg, cnt + 3)
