@@ -128,6 +128,7 @@ BIN_CASES = [
     (1, 70000, 16, 16, 16, 6),       # one list of 18275 > 16k: the in-place global sort
     (1, 3000, 640, 480, 8, 120),     # rects far above 64 tiles: the scatter repeats the reach test
     (2, 1500, 333, 250, 16, 90),     # mixed rect sizes around the 64-tile mask limit, ragged edges
+    (2, 3000, 1600, 1200, 8, 40),    # 30000 tiles per view: the histogram leaves shared memory (global atomics)
 ]
 
 
