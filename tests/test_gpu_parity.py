@@ -601,16 +601,26 @@ def test_graph_replay_matches_eager_and_is_deterministic():
     assert torch.equal(p0, graphed.params)
 
 
-def test_adam_matches_oracle():
+@pytest.mark.parametrize("offset", [0, 1])
+def test_adam_matches_oracle(offset):
+    """offset 0: 16-byte aligned arrays (float4 body plus a scalar tail, odd count);
+    offset 1: arrays that start one float into their allocations (the scalar kernel)."""
     torch = torch_cuda()
     N = native()
     rng = np.random.default_rng(1)
-    n, deg = 1001, 3                         # odd count: float4 body plus scalar tail
+    n, deg = 1001, 3
     P = N.cgs_param_count(n, deg)
     theta = rng.normal(size=P).astype(np.float32)
     lr6 = (1.6e-4, 5e-3, 1e-3, 2.5e-2, 2.5e-3, 1.25e-4)
     lam = 0.001
-    pt, mt, vt = (torch.from_numpy(theta).cuda(), torch.zeros(P, device="cuda"), torch.zeros(P, device="cuda"))
+
+    def dev_array(x):   # the array starts `offset` floats into its allocation
+        buf = torch.zeros(P + offset, device="cuda")
+        buf[offset:] = torch.from_numpy(x).cuda()
+        return buf[offset:]
+
+    pt, mt, vt = dev_array(theta), dev_array(np.zeros(P, np.float32)), dev_array(np.zeros(P, np.float32))
+    assert (pt.data_ptr() % 16 == 0) == (offset == 0)
     th, m, v = theta.astype(np.float64), np.zeros(P), np.zeros(P)
     lr = O.lr_per_element(n, deg, lr6)
     lo_dev = torch.zeros(1, device="cuda")
@@ -622,7 +632,7 @@ def test_adam_matches_oracle():
         gfull[10 * n: 11 * n] += greg
         lo_ref, _ = O.opacity_reg(th, n, lam)
         th, m, v = O.adam(th, gfull, m, v, step, lr)
-        N.cgs_adam(pt, torch.from_numpy(g).cuda(), mt, vt, n, deg, lr6, 0.9, 0.999, 1e-15, step, lam, lo_dev)
+        N.cgs_adam(pt, dev_array(g), mt, vt, n, deg, lr6, 0.9, 0.999, 1e-15, step, lam, lo_dev)
         torch.cuda.synchronize()
         # float32 storage of the parameters: a few ulps of |theta| plus 1e-5 of a step
         np.testing.assert_allclose(pt.cpu().numpy(), th, rtol=4 * 2.0 ** -24 * step, atol=1e-5 * max(lr6))
