@@ -36,10 +36,11 @@ namespace cgs {
 
 // Splats to which at most this many lanes of a warp contribute are added with per-lane
 // atomics (L2 reductions); more contributors go through the warp sum.  Measured on the
-// 16-view window with eight pixels per thread (raster backward ms): 4 lanes 3.94, 8 lanes
-// 3.87, 16 lanes 3.81, 20 lanes 3.93, 24 lanes 4.04; folding a half-warp onto the other
-// and adding from 16 lanes is twice as slow (same-address atomics serialise).
-constexpr int kDirectLanes = 16;
+// 16-view window with the persistent 28-warp kernel (raster backward ms): 4 lanes 3.366,
+// 8 lanes 3.347, 10 lanes 3.340, 12 lanes 3.344, 16 lanes 3.419, 20 lanes 3.580, 24 lanes
+// 3.877; folding a half-warp onto the other and adding from 16 lanes was twice as slow
+// (same-address atomics serialise).
+constexpr int kDirectLanes = 10;
 
 // Row stride (floats) of the per-warp reduction buffer: ten fields padded to 12.
 constexpr int kRedStride = 12;
