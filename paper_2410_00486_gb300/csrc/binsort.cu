@@ -4,7 +4,7 @@
 // tile.  Instead of a global LSD radix sort over 64-bit (tile, depth) keys, which
 // reads and writes every instance once per digit pass, the sort here is
 // most-significant-digit first with the tile id as one full-width digit:
-//   1. k_count_agg   : per (4096-slot chunk, tile) instance counts in shared memory; a
+//   1. k_count_agg   : per (slot chunk, tile) instance counts in shared memory; a
 //                      slot is counted in the tiles of its rect its alpha >= 1/255 ellipse
 //                      reaches (reach_box, over the tiles of the ellipse's bounding box),
 //                      and a slot with at most 64 such tiles keeps the decisions as a bit
@@ -35,9 +35,15 @@ constexpr int kBigThreads = 1024;
 constexpr int kBigCap = 16384;       // keys held in shared memory by the big-tile kernel
 constexpr uint64_t kPadKey = ~0ull;  // larger than any real key
 constexpr size_t kAggMaxSmem = 96 * 1024;   // per-view tile histogram in shared memory
-// Slots of a view per block of the count and scatter passes: 8192 measured 1% faster on the
-// 16-view window but 9% slower for one view at a time (half the blocks).
-constexpr int kChunk = 4096;
+// Slots of a view per block of the count and scatter passes: 2048, or 1024 when 2048 would
+// leave fewer than four blocks per SM.  Measured (whole sort, ms): the 16-view 300k window
+// 0.844 / 0.831 / 0.862 / 1.024 for 1024 / 2048 / 4096 / 8192; one 100k view 0.101 / 0.115 /
+// 0.153 (49 blocks of 2048 slots for 152 SMs).
+constexpr int kChunkLarge = 2048, kChunkSmall = 1024;
+static int chunk_for(int64_t n, int64_t V, int num_sms)
+{
+    return (n + kChunkLarge - 1) / kChunkLarge * V >= 4 * (int64_t)num_sms ? kChunkLarge : kChunkSmall;
+}
 
 // Scan of the per-tile counts: blocks of kScanThreads threads, kScanPer entries each.
 constexpr int kScanThreads = 1024, kScanPer = 4, kScanSpan = kScanThreads * kScanPer;
@@ -89,15 +95,16 @@ static size_t ws_layout(int64_t capacity, int64_t Ttot, int64_t chunk_counts, in
 
 // Per-(chunk, tile) counts kept between the count and scatter passes when a view's tile
 // histogram fits in shared memory.
-static int64_t chunk_count_entries(int64_t n, int64_t V, int64_t Tv)
+static int64_t chunk_count_entries(int64_t n, int64_t V, int64_t Tv, int chunk)
 {
     if (sizeof(uint32_t) * (size_t)Tv > kAggMaxSmem) return 0;
-    return (n + kChunk - 1) / kChunk * V * Tv;
+    return (n + chunk - 1) / chunk * V * Tv;
 }
 
-size_t bin_ws_bytes(int64_t capacity, int64_t n, int64_t V, int64_t Tv)
+size_t bin_ws_bytes(int64_t capacity, int64_t n, int64_t V, int64_t Tv, int num_sms)
 {
-    return ws_layout(capacity, Tv * V, chunk_count_entries(n, V, Tv), V * n, nullptr, nullptr);
+    return ws_layout(capacity, Tv * V, chunk_count_entries(n, V, Tv, chunk_for(n, V, num_sms)), V * n, nullptr,
+                     nullptr);
 }
 
 __device__ __forceinline__ bool load_slot(const float4 *__restrict__ rec, int64_t slot, float &u, float &v,
@@ -148,7 +155,7 @@ __global__ void k_count(const float4 *__restrict__ rec, int64_t n, int V, Grid g
 }
 
 // Shared-memory aggregated variants, used when a view's tile histogram fits in shared
-// memory: block (c, v) owns slots [c*kChunk, (c+1)*kChunk) of view v, counts its
+// memory: block (c, v) owns slots [c*chunk, (c+1)*chunk) of view v, counts its
 // instances per tile in shared memory and touches each global counter once.
 constexpr int kAggThreads = 512;
 // Three resident blocks per SM (at most 42 registers; the count pass needs 49 unbounded):
@@ -362,15 +369,15 @@ constexpr int kAggWarps = kAggThreads / 32;
 constexpr size_t kStageBytes = sizeof(PairStage) * kAggWarps;
 
 __global__ void __launch_bounds__(kAggThreads, kAggMinBlocks)
-k_count_agg(const float4 *__restrict__ rec, int64_t n, Grid g, uint32_t *__restrict__ count,
+k_count_agg(const float4 *__restrict__ rec, int64_t n, int chunk, Grid g, uint32_t *__restrict__ count,
             uint32_t *__restrict__ bcount, uint4 *__restrict__ slotrec)
 {
     extern __shared__ float4 smem_agg[];
     PairStage *stage = reinterpret_cast<PairStage *>(smem_agg);
     uint32_t *hist = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(smem_agg) + kStageBytes);
     const int view = blockIdx.y;
-    const int64_t s0 = (int64_t)blockIdx.x * kChunk;
-    const int64_t s1 = min(n, s0 + kChunk);
+    const int64_t s0 = (int64_t)blockIdx.x * chunk;
+    const int64_t s1 = min(n, s0 + chunk);
     __shared__ uint32_t next;
     for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) hist[t] = 0;
     if (threadIdx.x == 0) next = 0;
@@ -540,7 +547,7 @@ __global__ void k_scatter(const float4 *__restrict__ rec, int64_t n, int V, Grid
 // instances per tile again, reserves one contiguous run per tile in each bucket with a
 // single global atomic, then places its instances with shared-memory atomics.
 __global__ void __launch_bounds__(kAggThreads, kAggMinBlocks)
-k_scatter_agg(const float4 *__restrict__ rec, int64_t n, Grid g, const uint32_t *__restrict__ start,
+k_scatter_agg(const float4 *__restrict__ rec, int64_t n, int chunk, Grid g, const uint32_t *__restrict__ start,
               uint32_t *__restrict__ cursor, const uint32_t *__restrict__ bcount, uint4 *__restrict__ slotrec,
               uint64_t *__restrict__ keys, int64_t capacity)
 {
@@ -548,8 +555,8 @@ k_scatter_agg(const float4 *__restrict__ rec, int64_t n, Grid g, const uint32_t 
     PairStage *stage = reinterpret_cast<PairStage *>(smem_agg);
     uint32_t *hist = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(smem_agg) + kStageBytes);  // run positions
     const int view = blockIdx.y;
-    const int64_t s0 = (int64_t)blockIdx.x * kChunk;
-    const int64_t s1 = min(n, s0 + kChunk);
+    const int64_t s0 = (int64_t)blockIdx.x * chunk;
+    const int64_t s1 = min(n, s0 + chunk);
     // this chunk's per-tile counts (from the count pass): reserve one run per tile
     const int64_t tbase = (int64_t)view * g.Tv;
     const uint32_t *mine = bcount + ((int64_t)view * gridDim.x + blockIdx.x) * g.Tv;
@@ -900,7 +907,8 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
 {
     const int64_t Ttot = g.Tv * V;
     BinWs w{};
-    ws_layout(capacity, Ttot, chunk_count_entries(n, V, g.Tv), (int64_t)V * n, &w, ws);
+    const int chunk = chunk_for(n, V, num_sms);
+    ws_layout(capacity, Ttot, chunk_count_entries(n, V, g.Tv, chunk), (int64_t)V * n, &w, ws);
     const float4 *r4 = reinterpret_cast<const float4 *>(rec);
     cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (2 * (size_t)Ttot + 3), s);
     if (e != cudaSuccess) return e;
@@ -914,11 +922,11 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
             e = cudaFuncSetAttribute(k_scatter_agg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)agg_smem);
         if (e != cudaSuccess) return e;
     }
-    const dim3 agrid((unsigned)((n + kChunk - 1) / kChunk), (unsigned)V);
+    const dim3 agrid((unsigned)((n + chunk - 1) / chunk), (unsigned)V);
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((slots + threads - 1) / threads, (int64_t)num_sms * 16);
     if (agg)
-        k_count_agg<<<agrid, kAggThreads, agg_smem, s>>>(r4, n, g, w.count, w.bcount, w.slotrec);
+        k_count_agg<<<agrid, kAggThreads, agg_smem, s>>>(r4, n, chunk, g, w.count, w.bcount, w.slotrec);
     else
         k_count<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count);
     const int nsb = (int)((Ttot + kScanSpan - 1) / kScanSpan);
@@ -926,7 +934,7 @@ cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws
     k_scan_out<<<nsb, kScanThreads, 0, s>>>(w.count, Ttot, capacity, w.part, w.bhist, nsb, ranges, order, n_inst,
                                             w.nbig, status);
     if (agg)
-        k_scatter_agg<<<agrid, kAggThreads, agg_smem, s>>>(r4, n, g, w.count, w.cursor, w.bcount, w.slotrec,
+        k_scatter_agg<<<agrid, kAggThreads, agg_smem, s>>>(r4, n, chunk, g, w.count, w.cursor, w.bcount, w.slotrec,
                                                              w.keys, capacity);
     else
         k_scatter<<<blocks, threads, 0, s>>>(r4, n, V, g, w.count, w.cursor, w.keys, capacity);

@@ -10,7 +10,7 @@ cudaError_t preprocess_fwd(const float *P, int64_t n, int deg, const cgs_camera 
 cudaError_t preprocess_bwd(const float *P, int64_t n, int deg, const cgs_camera *cams, int V, const Grid &g,
                            float near_z, const float *rec, const float *sgrad, float *pgrad, int accumulate,
                            float *accum, float *denom, float *maxr, cudaStream_t s);
-size_t bin_ws_bytes(int64_t capacity, int64_t n, int64_t V, int64_t Tv);
+size_t bin_ws_bytes(int64_t capacity, int64_t n, int64_t V, int64_t Tv, int num_sms);
 cudaError_t bin_sort(const float *rec, int64_t n, int V, const Grid &g, void *ws, int64_t capacity, uint32_t *vals,
                      uint32_t *ranges, uint32_t *order, int64_t *n_inst, int32_t *status, int num_sms,
                      cudaStream_t s);
@@ -87,7 +87,7 @@ int cgs_preprocess(const float *params, int64_t n, const cgs_camera *cams, int32
 size_t cgs_bin_sort_workspace(int64_t capacity, int64_t n, int32_t V, const cgs_config *cfg)
 {
     if (!cfg_ok(cfg) || V < 1 || capacity < 0 || n < 1) return 0;
-    return bin_ws_bytes(capacity, n, V, make_grid(*cfg).Tv);
+    return bin_ws_bytes(capacity, n, V, make_grid(*cfg).Tv, num_sms());
 }
 
 int cgs_bin_sort(const float *rec, int64_t n, int32_t V, const cgs_config *cfg, void *workspace,
@@ -98,7 +98,7 @@ int cgs_bin_sort(const float *rec, int64_t n, int32_t V, const cgs_config *cfg, 
     if (capacity < 0 || capacity > 0xffffffffll || (capacity > 0 && !vals)) return CGS_ERR_ARG;
     if (((uintptr_t)workspace & 255) != 0 || !aligned16(rec)) return CGS_ERR_ARG;
     Grid g = make_grid(*cfg);
-    if (workspace_bytes < bin_ws_bytes(capacity, n, V, g.Tv)) return CGS_ERR_WORKSPACE;
+    if (workspace_bytes < bin_ws_bytes(capacity, n, V, g.Tv, num_sms())) return CGS_ERR_WORKSPACE;
     return cuda_status(bin_sort(rec, n, V, g, workspace, capacity, vals, ranges, tile_order, n_inst_dev,
                                 status_dev, num_sms(), (cudaStream_t)stream));
 }
