@@ -348,16 +348,15 @@ k_preprocess(const float *__restrict__ P, int64_t n, const cgs_camera *__restric
     }
 }
 
-// Backward of one visible slot: accumulates parameter gradients into the block's
-// shared accumulators (acc has the staged layout) with shared-memory atomics.
+// Backward of one visible slot: accumulates parameter gradients (and dL/dSigma, whose
+// chain to scale and rotation sigma_bwd runs once per Gaussian) into the block's shared
+// accumulators (acc has the staged layout) with shared-memory atomics.
 template <int DEG>
 __device__ __forceinline__ void project_bwd(const Staged &st, int gl, const float *cam, const Proj<DEG> &o,
                                             float4 G0, float4 G1, float4 G2, float *acc)
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    float *a_means = acc;
-    float *a_scales = acc + 3 * kGB;
-    float *a_quats = acc + 6 * kGB;
+    float *a_means = acc;   // scales and quaternions get theirs once per Gaussian (sigma_bwd)
     float *a_opac = acc + 10 * kGB;
     float *a_dc = acc + 11 * kGB;
     float *a_rest = acc + 14 * kGB;
