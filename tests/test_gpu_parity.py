@@ -564,7 +564,9 @@ def test_batched_equals_per_view():
     torch.testing.assert_close(a.loss_view, b.loss_view, rtol=1e-6, atol=0)
     param_grad_check(a.grads.cpu().numpy(), b.grads.cpu().numpy(), sc.n, 3, None, "batched vs per-view", l2=1e-5)
     assert torch.equal(a.denom, b.denom) and torch.equal(a.max_r2d, b.max_r2d)
-    torch.testing.assert_close(a.accum, b.accum, rtol=1e-5, atol=1e-12)
+    # the gradient norms summed into accum come from atomics in different orders: near-zero
+    # entries get a floor at 1e-5 of the largest
+    torch.testing.assert_close(a.accum, b.accum, rtol=1e-5, atol=1e-5 * b.accum.abs().max().item())
 
 
 def test_graph_replay_matches_eager_and_is_deterministic():
@@ -1185,4 +1187,10 @@ def test_paper_loop_equals_single_view_iterations():
     # atomics-order noise can flip the sign of a near-zero Adam step; nothing else differs
     assert (d > 1e-6).float().mean().item() < 1e-3
     assert d.max().item() <= 2 * sc.views * max(a.lr) + 1e-6
-    torch.testing.assert_close(a.m, b.m, rtol=1e-3, atol=1e-9)
+    # first moments: the two runs add the same float32 gradient terms in different orders
+    # (atomics), so an element whose terms cancel can differ by far more than 1e-3 of itself
+    # (a few in a million did, by up to 1.4e-7 against moments up to ~1e-3); bound the vector
+    # in L2 and the share of elements beyond the per-element bound, as for the parameters
+    dm = (a.m - b.m).abs()
+    assert (dm.norm() / b.m.norm()).item() < 1e-4
+    assert (dm > 1e-3 * b.m.abs() + 1e-9).float().mean().item() < 1e-3
