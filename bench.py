@@ -21,6 +21,7 @@ FP64 oracle timed on the host cores as a CPU baseline.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -236,7 +237,7 @@ def run_reference(args):
         return
     from oracle import oracle as O
     from synth import make_scene
-    sc = make_scene(args.config)
+    sc = dataclasses.replace(make_scene(args.config), tile=args.tile)   # the GPU arm's tile size
     cores = host_cores()
     O.set_threads(cores)
     rows = band_rows(sc)
@@ -263,7 +264,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded scene, no dataset)",
-        "config": workload_config(sc, {"tile": sc.tile}),
+        "config": arm_config(sc, args.tile, args.batch_depth, args.batch_depth_bwd, args.config),
         "ms_per_window": 1e3 * t_window, "wall_s": round(wall, 2),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"each step: a {rows}-row band of all {sc.views} views (bands of rows taken "
@@ -283,6 +284,15 @@ WORKLOAD_TEXT = {
     4: "synthetic room, TUM-like path with uneven visibility",
     5: "synthetic room, opacity logits N(-1,1.5)",
 }
+
+
+def arm_config(sc, tile, bd, bdb, config_index, extra=None):
+    """The `config` object of both arms' lines: the workload and the launch shape (measured
+    quantities such as the tile-instance count sit outside it)."""
+    cfg = workload_config(sc, {"tile": tile, "batch_depth": bd, "batch_depth_bwd": bdb, "config_index": config_index})
+    if extra:
+        cfg.update(extra)
+    return cfg
 
 
 def workload_config(sc, extra=None):
@@ -496,15 +506,13 @@ def main():
         cpu = cpu_baseline(sc)
 
     if rank == 0:
-        extra = {"tile": tile, "batch_depth": bd, "batch_depth_bwd": bdb, "tile_instances": ninst,
-                 "config_index": args.config}
-        if tuned:
-            extra["autotune"] = tuned
+        extra = {"autotune": tuned} if tuned else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scene)",
-            "config": workload_config(sc, extra),
+            "config": arm_config(sc, tile, bd, bdb, args.config, extra),
+            "tile_instances": ninst,
             "view_iters_per_s": value * V,
             "per_view_form": per_view,
             "paper_loop_form": paper_loop,

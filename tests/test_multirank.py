@@ -63,3 +63,8 @@ def test_reference_arm_under_torchrun_reports_once():
     assert d["impl"] == "reference" and d["value"] > 0 and d["n_gpus"] == 2
     assert d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+    # the same config object as the GPU arm's line at its default launch shape
+    sys.path.insert(0, str(ROOT))
+    import bench
+    from synth import make_scene
+    assert d["config"] == bench.arm_config(make_scene(1), 16, 128, 32, 1)
