@@ -184,8 +184,12 @@ __global__ void __launch_bounds__(B *B / ppt_for<B, kPPTBwd>(), (min_blocks_for<
                     pw[h] = power_at(pxs, q1.x, dyv[h]);
                     k[h] = pos < lst[p] && fabsf(pw[h]) <= q1.w;
                 }
-                if (!(k[0] || k[1])) continue;
-                contrib = true;
+                // a warp-uniform branch (vote) rather than a divergent one: a lane whose pair
+                // blends nothing runs the pair with alpha = 0, which changes nothing (3.337 ->
+                // 3.297 ms on the 16-view window)
+                const bool pair = k[0] || k[1];
+                contrib = contrib || pair;
+                if (!__any_sync(kFull, pair)) continue;
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
                     const int p = p2 + h;
