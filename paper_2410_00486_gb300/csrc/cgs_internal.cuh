@@ -148,21 +148,21 @@ __device__ __forceinline__ ReachPre reach_prepare(float A, float B, float C, flo
 __device__ __forceinline__ bool reach_box(const ReachPre &p, float u, float v, float bx0, float bx1, float by0,
                                           float by1)
 {
-    if (p.mode != 2) return p.mode == 1;
-    const float dx = fabsf(__fsub_rn(u, fminf(fmaxf(u, bx0), bx1)));
-    const float dy = fabsf(__fsub_rn(v, fminf(fmaxf(v, by0), by1)));
-    if (!(dx <= p.ex && dy <= p.ey)) return false;
-    if (dx == 0.f && dy == 0.f) return true;
+    // computed without early returns (the lanes of a warp test different tiles): the box
+    // check, the centre inside the box, and the minimum over the edges facing the centre
+    const float ddx0 = __fsub_rn(u, fminf(fmaxf(u, bx0), bx1));
+    const float ddy1 = __fsub_rn(v, fminf(fmaxf(v, by0), by1));
+    const float dx = fabsf(ddx0), dy = fabsf(ddy1);
     // q is convex with its minimum at the centre, outside the box: its minimum over the box
     // lies on an edge facing the centre, the vertical edge at the clamped x or the
     // horizontal edge at the clamped y (where the centre is inside the box's x (y) range,
     // that "edge" evaluation gives q at a point of the box, which is no lower than the
     // minimum)
-    const float ddx0 = __fsub_rn(u, fminf(fmaxf(u, bx0), bx1));
     const float ddy0 = fminf(fmaxf(-__fmul_rn(p.bc, ddx0), __fsub_rn(v, by1)), __fsub_rn(v, by0));
-    const float ddy1 = __fsub_rn(v, fminf(fmaxf(v, by0), by1));
     const float ddx1 = fminf(fmaxf(-__fmul_rn(p.ba, ddy1), __fsub_rn(u, bx1)), __fsub_rn(u, bx0));
-    return fminf(edge_q(p.A, p.B2, p.C, ddx0, ddy0), edge_q(p.A, p.B2, p.C, ddx1, ddy1)) <= p.t2;
+    const bool edge = fminf(edge_q(p.A, p.B2, p.C, ddx0, ddy0), edge_q(p.A, p.B2, p.C, ddx1, ddy1)) <= p.t2;
+    const bool reach = dx <= p.ex && dy <= p.ey && ((dx == 0.f && dy == 0.f) || edge);
+    return p.mode == 2 ? reach : p.mode == 1;
 }
 
 constexpr float kAlphaMax = 0.99f;
