@@ -562,9 +562,24 @@ k_scatter_agg(const float4 *__restrict__ rec, int64_t n, int chunk, Grid g, cons
     const uint32_t *mine = bcount + ((int64_t)view * gridDim.x + blockIdx.x) * g.Tv;
     __shared__ uint32_t next;
     if (threadIdx.x == 0) next = 0;
-    for (int t = threadIdx.x; t < g.Tv; t += blockDim.x) {
-        const uint32_t c = mine[t];
-        hist[t] = c ? start[tbase + t] + atomicAdd(cursor + tbase + t, c) : 0u;
+    for (int t0 = threadIdx.x; t0 < g.Tv; t0 += 4 * blockDim.x) {   // four tiles in flight
+        uint32_t c[4], st4[4], r[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int t = t0 + q * (int)blockDim.x;
+            c[q] = t < g.Tv ? mine[t] : 0u;
+            st4[q] = t < g.Tv ? start[tbase + t] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int t = t0 + q * (int)blockDim.x;
+            r[q] = c[q] ? atomicAdd(cursor + tbase + t, c[q]) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int t = t0 + q * (int)blockDim.x;
+            if (t < g.Tv) hist[t] = c[q] ? st4[q] + r[q] : 0u;
+        }
     }
     __syncthreads();
     for_each_tile_pair<false>(rec, n, view, s0, s1, g, &next, stage[threadIdx.x >> 5], slotrec,
@@ -696,12 +711,23 @@ __device__ __forceinline__ void sort_tile(SortSmem<NTH, CAP> &sm, const uint64_t
     // load, and find the range of the depth bits over the tile (positive floats: the bits
     // order like the values)
     uint32_t dmin = ~0u, dmax = 0u;
-    for (uint32_t i = threadIdx.x; i < len; i += NTH) {
-        const uint64_t k = keys[st + i];
-        bufA[i] = k;
-        const uint32_t d = (uint32_t)(k >> 32);
-        dmin = min(dmin, d);
-        dmax = max(dmax, d);
+    for (uint32_t i0 = threadIdx.x; i0 < len; i0 += 4 * NTH) {   // four keys in flight
+        uint64_t kk[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint32_t i = i0 + q * NTH;
+            kk[q] = i < len ? keys[st + i] : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint32_t i = i0 + q * NTH;
+            if (i < len) {
+                bufA[i] = kk[q];
+                const uint32_t dd = (uint32_t)(kk[q] >> 32);
+                dmin = min(dmin, dd);
+                dmax = max(dmax, dd);
+            }
+        }
     }
     for (int off = 16; off > 0; off >>= 1) {
         dmin = min(dmin, __shfl_xor_sync(kFull, dmin, off));
