@@ -288,6 +288,72 @@ def test_bin_sort_depth_ties_bit_exact(extra):
             check_culled_lists(g.cpu().numpy().reshape(-1, 12), ranges_o, vals_o, rg, vv, W, H, B)
 
 
+def sort_path_of_tiles(z32, ranges, vals, bits=11, work=32):
+    """Per tile with at least two keys, whether the per-tile sort takes its bucket pass:
+    buckets by the top `bits` of the depth bits less the tile's smallest, and the sum of
+    squared bucket sizes at most `work` per key (else the radix sort)."""
+    d = np.asarray(z32, np.float32).view(np.uint32).astype(np.int64)
+    out = []
+    for s0, s1 in ranges:
+        if s1 - s0 < 2:
+            continue
+        r = d[vals[s0:s1]]
+        r = r - r.min()
+        sh = max(0, int(r.max()).bit_length() - bits)
+        c = np.bincount(r >> sh).astype(np.int64)
+        out.append(int((c * c).sum()) <= work * (s1 - s0))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("extra", [0, 1100])
+def test_bin_sort_bucket_and_radix_paths_bit_exact(extra):
+    """Tiles of both per-tile sort paths in one launch: spread depths (the bucket pass: a
+    histogram over the top bits of the tile's depth range, then ranks within each bucket),
+    and a tile whose 400 depths crowd into one bucket because a near splat widens its range
+    (the radix sort); 100 depths in equal pairs a few ulps apart share a bucket on the bucket
+    path.  With
+    `extra` the crowded tile passes 1024 keys (the eight-warp kernel).  Lists equal the
+    oracle's bit for bit."""
+    torch = torch_cuda()
+    N = native()
+    rng = np.random.default_rng(57)
+    W, H, B = 64, 48, 16
+    n = 2400 + extra
+    u = rng.uniform(0, W, n)
+    v = rng.uniform(0, H, n)
+    r = rng.integers(1, 6, n).astype(np.int32)
+    z = rng.uniform(0.5, 50.0, n).astype(np.float32)
+    # tile (0, 0): one near splat and 400 (+ extra) depths within 0.1% of 20
+    u[0], v[0], r[0], z[0] = 8.0, 8.0, 3, 0.3
+    m = 401 + extra
+    u[1:m], v[1:m], r[1:m] = rng.uniform(5, 11, m - 1), rng.uniform(5, 11, m - 1), 2
+    z[1:m] = (20.0 * (1.0 + 1e-3 * rng.random(m - 1))).astype(np.float32)
+    # tile (2, 1): 100 depths in pairs of equal values a few ulps apart, one bucket of a
+    # wide range, which stays on the bucket path: ranks by the full key (depth, then slot)
+    c0 = m
+    u[c0:c0 + 100], v[c0:c0 + 100], r[c0:c0 + 100] = rng.uniform(37, 43, 100), rng.uniform(21, 27, 100), 2
+    z[c0:c0 + 100] = np.float32(7.0) + (np.arange(100) // 2).astype(np.float32) * np.spacing(np.float32(7.0))
+    conic = np.zeros((n, 3), np.float32)
+    conic[:, 0] = conic[:, 2] = (3.0 / r.astype(np.float32)) ** 2
+    rec10 = np.zeros((n, 10))
+    rec10[:, 0], rec10[:, 1], rec10[:, 9] = u, v, z
+    rec10[:, 2:5], rec10[:, 5] = conic, 0.9
+    g = rec_to_gpu(rec10, r)
+    ranges_o, vals_o = O.bin_lists(u, v, z.astype(np.float64), r, 1, n, W, H, B)
+    lens = ranges_o[:, 1].astype(np.int64) - ranges_o[:, 0]
+    assert lens.max() < 2048 and (lens[0] > 1024) == (extra > 0)
+    path = sort_path_of_tiles(z, ranges_o, vals_o)
+    assert path.any() and not path.all()           # both paths occur
+    assert not sort_path_of_tiles(z, ranges_o[:1], vals_o)[0]   # the crowded tile: radix
+    assert sort_path_of_tiles(z, ranges_o[6:7], vals_o)[0]      # the 100-key bucket: ranks
+    cfg = N.make_config(W, H, B, 64, 0, rect_lists=True)
+    vals, ranges, _, ninst, st = gpu_bin(N, g, n, 1, cfg, len(vals_o) + 3)
+    assert st == 0 and ninst == len(vals_o)
+    rg, vv = gpu_lists(vals, ranges, ninst)
+    assert np.array_equal(rg, ranges_o) and np.array_equal(vv, vals_o)
+    print(f"[bin sort paths extra={extra}] tiles {len(path)}, bucket pass {int(path.sum())}, radix {int((~path).sum())}")
+
+
 def test_bin_sort_capacity_overflow_reports_and_truncates():
     torch = torch_cuda()
     N = native()
