@@ -689,8 +689,8 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *wsum)
 // shares the radix sort's digit histograms and ranks, which the long-list kernel's 2048
 // buckets fit).  A tile is bucket-sorted when its rank work, the sum over buckets of the
 // squared bucket size, is at most kRankWork per key; else it takes the radix sort.  On the
-// 16-view window the bucket sort took the whole bin sort from 0.803 to 0.760 ms (16 per
-// key: 0.769, 64: 0.760), lists identical.
+// 16-view window the bucket sort took the whole bin sort from 0.803 to 0.755 ms, lists
+// identical (a bound of 16 per key: 0.769 ms; 64 as fast as 32).
 constexpr int kBucketBits = 11, kBuckets = 1 << kBucketBits;
 constexpr uint32_t kRankWork = 32;
 
