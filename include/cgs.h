@@ -192,7 +192,7 @@ int cgs_render_fwd(const float *rec, const uint32_t *vals, const uint32_t *range
 /*
  * cgs_render_fwd_noalloc -- cgs_render_fwd for callers that cannot allocate device
  * memory or pass a workspace: for instance a real-time mapping loop that must not
- * allocate once running (an allocation can block on the driver and miss the frame
+ * allocate once running (an allocation can block in the CUDA driver and miss the frame
  * budget), or glue code that only receives another framework's input and output
  * buffers.  The paper has no counterpart; it is an interface convenience.
  * Same arguments and results as cgs_render_fwd without the workspace.  The per-tile

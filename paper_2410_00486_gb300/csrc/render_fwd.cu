@@ -269,7 +269,7 @@ cudaError_t loss_reduce(const float *partials, const Grid &g, int V, const float
 // cgs_render_fwd_noalloc: the forward render with its scratch inside the library.
 //
 // Some callers cannot hand the library a workspace: a real-time mapping thread that
-// must not allocate once it is running (a device allocation can block on the driver
+// must not allocate once it is running (a device allocation can block in the CUDA driver
 // and miss the frame budget), or code that only ever sees the input and output
 // buffers of another framework.  For them the per-tile partial sums live in this
 // file-scope device array, sized for kNoAllocMaxTiles tiles (V * tiles per view);
